@@ -1,0 +1,314 @@
+"""Seeded synthetic inputs: SU(3) gauge fields and fermion sources.
+
+This module is shared by the CPU oracle, the tests and the benchmark.  It
+holds none of the Schur-complement method's arithmetic (no Dirac operator,
+no site permutation, no Krylov solver); it only manufactures the background
+gauge fields and right-hand sides the method is applied to.
+
+The paper computes its Schur complements "in a SU(3) background field using
+the plaquette action" at beta = 5.4, 5.7, 5.9 (Section 1, around Fig. 2, and
+Section 4, Table 1).  Those ensembles are not available, so three seeded
+stand-ins are produced here:
+
+* ``random_gauge``: U = exp(i eps H), H traceless Hermitian with Gaussian
+  entries (a rough field whose roughness is set by eps);
+* ``ape_smear``: APE smearing of a field, projected back to SU(3);
+* ``heatbath_gauge``: the plaquette (Wilson) action sampled by a
+  Cabibbo-Marinari pseudo-heatbath over the three SU(2) subgroups, each SU(2)
+  drawn with the Kennedy-Pendleton algorithm (Phys. Lett. B156 (1985) 393).
+
+Layout conventions (shared with the CUDA library by agreement, not code):
+
+* lattice extents ``dims = (L0, L1, L2, L3)``; site index
+  ``s = x0 + L0*(x1 + L1*(x2 + L2*x3))`` (x0 fastest);
+* gauge field ``U`` is complex128 of shape ``(V, 4, 3, 3)``: ``U[s, mu]`` is the
+  3x3 matrix on the link from site s to s + mu-hat, row-major (row = first
+  colour index);
+* spinor fields are complex128 of shape ``(V, 4, 3)``: ``[site][spin][colour]``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "volume",
+    "random_gauge",
+    "ape_smear",
+    "heatbath_gauge",
+    "average_plaquette",
+    "gaussian_source",
+    "point_sources",
+    "random_su3",
+]
+
+
+def volume(dims) -> int:
+    v = 1
+    for L in dims:
+        v *= int(L)
+    return v
+
+
+# ---------------------------------------------------------------------------
+# lattice helpers (pure data movement on the (L3, L2, L1, L0, ...) grid)
+# ---------------------------------------------------------------------------
+
+def _to_grid(U, dims):
+    L0, L1, L2, L3 = dims
+    return U.reshape(L3, L2, L1, L0, *U.shape[1:])
+
+
+def _shift(F, mu, step):
+    """F(x + step*mu-hat) on a grid array with axes (x3, x2, x1, x0, ...)."""
+    axis = 3 - mu
+    return np.roll(F, -step, axis=axis)
+
+
+def _dag(M):
+    return np.conj(np.swapaxes(M, -1, -2))
+
+
+def _parity_mask(dims):
+    L0, L1, L2, L3 = dims
+    x3, x2, x1, x0 = np.meshgrid(np.arange(L3), np.arange(L2), np.arange(L1),
+                                 np.arange(L0), indexing="ij")
+    return ((x0 + x1 + x2 + x3) % 2).astype(np.int8)
+
+
+# ---------------------------------------------------------------------------
+# exp(i eps H)
+# ---------------------------------------------------------------------------
+
+def _traceless_hermitian(A):
+    H = 0.5 * (A + _dag(A))
+    tr = np.trace(H, axis1=-2, axis2=-1)
+    return H - (tr / 3.0)[..., None, None] * np.eye(3)
+
+
+def _expi_hermitian(H, eps):
+    w, v = np.linalg.eigh(H)
+    ph = np.exp(1j * eps * w)
+    return np.einsum("...ij,...j,...kj->...ik", v, ph, np.conj(v))
+
+
+def random_gauge(dims, eps, seed) -> np.ndarray:
+    """U_mu(x) = exp(i eps H_mu(x)), H traceless Hermitian from Gaussian A.
+
+    A has i.i.d. N(0,1) real and imaginary parts, drawn from
+    ``numpy.random.default_rng(seed)`` as one array of shape
+    (2, L3, L2, L1, L0, 4, 3, 3): index 0 is the real part, 1 the imaginary.
+    H = (A + A^dagger)/2 - tr(.)/3.  The exponential is taken through ``eigh``.
+    """
+    L0, L1, L2, L3 = dims
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((2, L3, L2, L1, L0, 4, 3, 3))
+    A = g[0] + 1j * g[1]
+    U = _expi_hermitian(_traceless_hermitian(A), eps)
+    return np.ascontiguousarray(U.reshape(volume(dims), 4, 3, 3))
+
+
+def random_su3(shape, seed) -> np.ndarray:
+    """Haar-ish random SU(3) matrices (QR of a complex Gaussian, phase-fixed)."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((2, *shape, 3, 3))
+    Z = g[0] + 1j * g[1]
+    Q, R = np.linalg.qr(Z)
+    d = np.diagonal(R, axis1=-2, axis2=-1)
+    Q = Q * (d / np.abs(d))[..., None, :]
+    det = np.linalg.det(Q)
+    return Q / (det ** (1.0 / 3.0))[..., None, None]
+
+
+# ---------------------------------------------------------------------------
+# APE smearing
+# ---------------------------------------------------------------------------
+
+def _project_su3(M):
+    """Nearest unitary by polar decomposition, then remove the phase of det."""
+    u, _, vh = np.linalg.svd(M)
+    W = u @ vh
+    det = np.linalg.det(W)
+    return W * np.exp(-1j * np.angle(det) / 3.0)[..., None, None]
+
+
+def ape_smear(U, dims, alpha, steps) -> np.ndarray:
+    """APE smearing, ``steps`` times:
+
+    U'_mu(x) = Proj_SU(3)[ (1 - alpha) U_mu(x) + alpha/6 * sum_{nu != mu} C_mu,nu(x) ]
+
+    with the two staples C = U_nu(x) U_mu(x+nu) U_nu(x+mu)^dagger
+    + U_nu(x-nu)^dagger U_mu(x-nu) U_nu(x-nu+mu).  All directions are updated
+    from the same old field in each step.
+    """
+    G = _to_grid(np.asarray(U, dtype=np.complex128), dims).copy()
+    for _ in range(int(steps)):
+        new = np.empty_like(G)
+        for mu in range(4):
+            C = np.zeros(G.shape[:4] + (3, 3), dtype=np.complex128)
+            for nu in range(4):
+                if nu == mu:
+                    continue
+                Un = G[..., nu, :, :]
+                Um = G[..., mu, :, :]
+                up = Un @ _shift(Um, nu, 1) @ _dag(_shift(Un, mu, 1))
+                Un_m = _shift(Un, nu, -1)
+                dn = _dag(Un_m) @ _shift(Um, nu, -1) @ _shift(Un_m, mu, 1)
+                C += up + dn
+            new[..., mu, :, :] = _project_su3((1.0 - alpha) * G[..., mu, :, :]
+                                              + (alpha / 6.0) * C)
+        G = new
+    return np.ascontiguousarray(G.reshape(volume(dims), 4, 3, 3))
+
+
+# ---------------------------------------------------------------------------
+# plaquette-action pseudo-heatbath
+# ---------------------------------------------------------------------------
+
+def _staple_sum(G, mu):
+    """A_mu(x) with Re tr(U_mu(x) A_mu(x)) = sum of the 6 plaquettes through the link."""
+    A = np.zeros(G.shape[:4] + (3, 3), dtype=np.complex128)
+    Um = G[..., mu, :, :]
+    for nu in range(4):
+        if nu == mu:
+            continue
+        Un = G[..., nu, :, :]
+        # forward: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+        A += _shift(Un, mu, 1) @ _dag(_shift(Um, nu, 1)) @ _dag(Un)
+        # backward: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
+        Un_m = _shift(Un, nu, -1)
+        A += _dag(_shift(Un_m, mu, 1)) @ _dag(_shift(Um, nu, -1)) @ Un_m
+    return A
+
+
+def _kp_sample_x0(alpha, rng):
+    """Kennedy-Pendleton: x0 in [-1, 1] with density ~ sqrt(1 - x0^2) exp(alpha x0)."""
+    n = alpha.shape[0]
+    out = np.empty(n)
+    todo = np.arange(n)
+    while todo.size:
+        a = alpha[todo]
+        r1 = 1.0 - rng.random(todo.size)
+        r2 = rng.random(todo.size)
+        r3 = 1.0 - rng.random(todo.size)
+        r4 = rng.random(todo.size)
+        delta = -(np.log(r1) + np.cos(2.0 * np.pi * r2) ** 2 * np.log(r3)) / a
+        ok = r4 * r4 <= 1.0 - 0.5 * delta
+        out[todo[ok]] = 1.0 - delta[ok]
+        todo = todo[~ok]
+    return out
+
+
+def _su2_heatbath_update(Ulinks, A, beta, rng, sub):
+    """One Cabibbo-Marinari SU(2) subgroup update of a batch of SU(3) links.
+
+    Ulinks, A: (n, 3, 3).  Returns the updated links.
+    """
+    i, j = sub
+    W = Ulinks @ A
+    w00, w01, w10, w11 = W[:, i, i], W[:, i, j], W[:, j, i], W[:, j, j]
+    a0 = 0.5 * (w00 + w11).real
+    a3 = 0.5 * (w00 - w11).imag
+    a2 = 0.5 * (w01 - w10).real
+    a1 = 0.5 * (w01 + w10).imag
+    k = np.sqrt(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3)
+    k = np.maximum(k, 1e-300)
+    x0 = _kp_sample_x0(2.0 * beta * k / 3.0, rng)
+    # uniform direction for the remaining three components
+    rad = np.sqrt(np.maximum(0.0, 1.0 - x0 * x0))
+    cth = 2.0 * rng.random(x0.shape[0]) - 1.0
+    phi = 2.0 * np.pi * rng.random(x0.shape[0])
+    sth = np.sqrt(1.0 - cth * cth)
+    x1 = rad * sth * np.cos(phi)
+    x2 = rad * sth * np.sin(phi)
+    x3 = rad * cth
+    # quaternion product x * what^dagger, what = (a0, a1, a2, a3)/k
+    b0, b1, b2, b3 = a0 / k, -a1 / k, -a2 / k, -a3 / k
+    r0 = x0 * b0 - x1 * b1 - x2 * b2 - x3 * b3
+    r1 = x0 * b1 + x1 * b0 - x2 * b3 + x3 * b2
+    r2 = x0 * b2 + x2 * b0 - x3 * b1 + x1 * b3
+    r3 = x0 * b3 + x3 * b0 - x1 * b2 + x2 * b1
+    # embedded 2x2: r0 + i (r1 s1 + r2 s2 + r3 s3)
+    R = np.empty((x0.shape[0], 2, 2), dtype=np.complex128)
+    R[:, 0, 0] = r0 + 1j * r3
+    R[:, 0, 1] = r2 + 1j * r1
+    R[:, 1, 0] = -r2 + 1j * r1
+    R[:, 1, 1] = r0 - 1j * r3
+    rows = Ulinks[:, [i, j], :]
+    out = Ulinks.copy()
+    out[:, [i, j], :] = R @ rows
+    return out
+
+
+def heatbath_gauge(dims, beta, sweeps, seed, start=None) -> np.ndarray:
+    """Quenched SU(3) field from the Wilson plaquette action at coupling beta.
+
+    Cold start (all links = 1) unless ``start`` is given; each sweep visits
+    mu = 0..3 and, for each mu, the even then the odd sites (checkerboard:
+    links of one direction on one parity share no staple), and performs the
+    three Cabibbo-Marinari subgroup updates (0,1), (1,2), (0,2).  All L_mu
+    must be even.  Random numbers come from ``numpy.random.default_rng(seed)``.
+    """
+    if any(int(L) % 2 for L in dims):
+        raise ValueError("heatbath checkerboard needs even extents")
+    rng = np.random.default_rng(seed)
+    V = volume(dims)
+    if start is None:
+        G = np.broadcast_to(np.eye(3, dtype=np.complex128),
+                            (V, 4, 3, 3)).copy()
+    else:
+        G = np.array(start, dtype=np.complex128, copy=True)
+    G = _to_grid(G, dims)
+    par = _parity_mask(dims)
+    for _ in range(int(sweeps)):
+        for mu in range(4):
+            for p in (0, 1):
+                A = _staple_sum(G, mu)
+                sel = par == p
+                links = G[..., mu, :, :][sel]
+                As = A[sel]
+                for sub in ((0, 1), (1, 2), (0, 2)):
+                    links = _su2_heatbath_update(links, As, beta, rng, sub)
+                Gm = G[..., mu, :, :]
+                Gm[sel] = links
+                G[..., mu, :, :] = Gm
+        # keep the links unitary against rounding drift
+        G = _project_su3(G)
+    return np.ascontiguousarray(G.reshape(V, 4, 3, 3))
+
+
+def average_plaquette(U, dims) -> float:
+    """<(1/3) Re tr U_mu,nu(x)> over sites and the 6 planes (a checksum)."""
+    G = _to_grid(np.asarray(U), dims)
+    tot = 0.0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            Um, Un = G[..., mu, :, :], G[..., nu, :, :]
+            P = Um @ _shift(Un, mu, 1) @ _dag(_shift(Um, nu, 1)) @ _dag(Un)
+            tot += np.trace(P, axis1=-2, axis2=-1).real.mean() / 3.0
+    return tot / 6.0
+
+
+# ---------------------------------------------------------------------------
+# sources
+# ---------------------------------------------------------------------------
+
+def gaussian_source(dims, seed, n_src=1) -> np.ndarray:
+    """Complex Gaussian source(s): re and im parts i.i.d. N(0,1).
+
+    Drawn as one array of shape (2, n_src, V, 4, 3).  Returns (V, 4, 3) for
+    n_src == 1, else (n_src, V, 4, 3).
+    """
+    V = volume(dims)
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((2, n_src, V, 4, 3))
+    src = g[0] + 1j * g[1]
+    return src[0] if n_src == 1 else src
+
+
+def point_sources(dims, site=0) -> np.ndarray:
+    """The 12 spin-colour point sources delta_{x,site} delta_{a,spin} delta_{i,col}."""
+    V = volume(dims)
+    out = np.zeros((12, V, 4, 3), dtype=np.complex128)
+    for k in range(12):
+        out[k, site, k // 3, k % 3] = 1.0
+    return out
