@@ -1,0 +1,169 @@
+/*
+ * gschur.h -- C ABI of the GB300 library for the gauged renormalisation-group
+ * step of lattice Wilson fermions: the Schur complement
+ *
+ *     S_bb = D_bb - D_br D_rr^-1 D_rb
+ *
+ * of the SU(3) Wilson-Dirac operator D after a site permutation puts the
+ * coarse sites b first (Boric, "On Gauged Renormalisation Group
+ * Transformations of Lattice Fermions", Section 1: the 2x2 partition, the
+ * Schur complement and its block UL factorisation; Section 2: the Type I /
+ * Type II permutations and their inverses).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: extents dims[4] = {L0, L1, L2, L3}, periodic; site index
+ *   s = x0 + L0*(x1 + L1*(x2 + L2*x3))   (x0 fastest).
+ * Gauge field: complex128 (interleaved re, im doubles) [V][4][3][3];
+ *   element [s][mu][a][b] is row a, column b of U_mu(x), the link from s to
+ *   s + mu-hat.
+ * Spinors: complex128 [n_sites][4][3] ([site][spin][colour]), 192 bytes a
+ *   site.  "Site order" = the lattice order above; "label order" = the order
+ *   of the permuted operator P D P^T, entry i being the site perm[i].
+ *   Vectors on the coarse set b are the first n_b labels; vectors on the rest
+ *   r are labels n_b .. V-1.
+ * Operator (Wilson parameter r = 1, gamma matrices in the DeGrand-Rossi
+ *   chiral basis, gamma_5 = diag(1, 1, -1, -1), direction mu <-> gamma_{mu+1}):
+ *   (D psi)(x) = (m0 + 4) psi(x) - 1/2 sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                   + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ].
+ * Permutations (p lists the label order; (P x)_i = x_{p(i)}):
+ *   GS_TYPE_I : b = sites with every coordinate even (n_b = V/16), stable.
+ *   GS_TYPE_II: b = sites with x_dir even (n_b = V/2), stable; one
+ *               direction per renormalisation step.
+ *   inverse != 0 uses q = p^-1 (operator P^T) with the same n_b.
+ *
+ * Memory: every pointer argument named *_dev is a device pointer owned by
+ * the caller (any allocator, e.g. PyTorch); the library never frees it and
+ * does not keep it past the call.  The library owns the context's own device
+ * memory (index tables, packed links, solver workspaces).
+ * Streams: all work is enqueued on the stream given to gs_create (a
+ * cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
+ * that return solver statistics synchronise that stream; the others are
+ * asynchronous.
+ * Errors: every call returns a gs_status; GS_OK is 0.  On failure
+ * gs_last_error() describes the cause.  No call aborts the process.
+ * A context is not thread-safe; use one context per host thread.
+ */
+#ifndef GSCHUR_H
+#define GSCHUR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gs_ctx gs_ctx;
+
+typedef enum {
+    GS_OK = 0,
+    GS_EINVAL = 1,     /* bad argument (sizes, type, null pointer, odd extent) */
+    GS_ENOMEM = 2,     /* device or host allocation failed */
+    GS_MAXITER = 3,    /* solver stopped at its iteration limit; result = last iterate */
+    GS_BREAKDOWN = 4,  /* Krylov breakdown (a zero inner product) */
+    GS_NONFINITE = 5,  /* NaN or Inf met in a solver scalar */
+    GS_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+    GS_ECUDA = 7,      /* a CUDA runtime call failed */
+    GS_ENOGAUGE = 8    /* no gauge field set yet */
+} gs_status;
+
+enum { GS_TYPE_I = 1, GS_TYPE_II = 2 };
+enum { GS_F64 = 0, GS_F32 = 1, GS_BF16 = 2 };
+enum { GS_GMRES = 0, GS_BICGSTAB = 1 };
+
+/* Options of schur_apply / schur_solve.  gs_default_opts fills the defaults
+ * in brackets. */
+typedef struct {
+    double tol;            /* outer: relative residual ||w_b - S_bb x_b|| / ||w_b|| [1e-10] */
+    int    max_iter;       /* outer: Arnoldi / BiCGStab steps in total [3000] */
+    int    restart;        /* GMRES(m) restart length m, 1..64 [30] */
+    int    outer_solver;   /* GS_GMRES or GS_BICGSTAB [GS_GMRES] */
+    double inner_tol;      /* inner: ||t - D_rr z|| / ||t|| for each D_rr^-1 [1e-12] */
+    int    inner_max_iter; /* inner: BiCGStab iterations per solve [5000] */
+    int    inner_prec;     /* arithmetic of the inner D_rr solve: GS_F64 [GS_F64] */
+    int    check_every;    /* inner convergence is read back every k iterations [4] */
+} gs_solve_opts;
+
+/* Statistics written by schur_apply / schur_solve (may be NULL). */
+typedef struct {
+    int       status;          /* gs_status of the call */
+    int       outer_iters;     /* Arnoldi (or BiCGStab) steps of the outer solve */
+    int       inner_solves;    /* number of D_rr^-1 applications */
+    long long inner_iters;     /* BiCGStab iterations summed over inner solves */
+    int       inner_max_seen;  /* largest single inner iteration count */
+    double    outer_residual;  /* final ||w_b - S_bb x_b|| / ||w_b|| (recursive estimate) */
+    double    true_residual;   /* schur_solve: ||f - D x|| / ||f|| recomputed in FP64 */
+    double    inner_residual;  /* largest final inner relative residual seen */
+    long long stencil_sites;   /* output sites of all stencil launches (work counter) */
+    long long kernel_launches; /* kernels enqueued by the call */
+} gs_solve_stats;
+
+/* Create a context for a dims[0] x dims[1] x dims[2] x dims[3] periodic
+ * lattice with bare mass m0 (kappa = 1/(2 m0 + 8)).  Every extent must be
+ * >= 2; V must be < 2^31 / 12.  stream: a cudaStream_t or NULL. */
+gs_status gs_create(gs_ctx** ctx_out, const int dims[4], double m0, void* stream);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+gs_status gs_destroy(gs_ctx* ctx);
+
+/* Copy the gauge field U_dev (complex128 [V][4][3][3], site order) into the
+ * context's packed link arrays.  U_dev is read during the call only.  Any
+ * permutation plan built before is repacked. */
+gs_status gs_set_gauge(gs_ctx* ctx, const void* U_dev);
+
+/* Fill opts with the defaults listed in gs_solve_opts. */
+void gs_default_opts(gs_solve_opts* opts);
+
+/* y = D x on the full lattice, site order (the Wilson-Dirac operator above,
+ * the operator the paper blocks).  x_dev, y_dev: complex128 [V][4][3]; must
+ * not overlap.  Asynchronous. */
+gs_status wilson_apply(gs_ctx* ctx, const void* x_dev, void* y_dev);
+
+/* Site permutation of Section 2 ("Permutation_block": P(p) exchanges the
+ * rows of D, coarse sites labelled first).
+ *   transpose == 0: y = P x,   y[i] = x[perm[i]]   (site order -> label order)
+ *   transpose != 0: y = P^T x, y[perm[i]] = x[i]   (label order -> site order)
+ * perm is p (inverse == 0) or q = p^-1 (inverse != 0) of the given type and
+ * direction (dir is used by GS_TYPE_II only, 0..3).  x_dev, y_dev: complex128
+ * [V][4][3], not overlapping.  *n_b_out (may be NULL) receives n_b.
+ * Asynchronous. */
+gs_status permute_sites(gs_ctx* ctx, int type, int dir, int inverse, int transpose,
+                        const void* x_dev, void* y_dev, int64_t* n_b_out);
+
+/* The label order itself: perm_dev (int32 [V], device) receives perm, i.e.
+ * perm_dev[i] = the site at label i.  *n_b_out (may be NULL) receives n_b.
+ * Asynchronous. */
+gs_status gs_get_permutation(gs_ctx* ctx, int type, int dir, int inverse,
+                             int32_t* perm_dev, int64_t* n_b_out);
+
+/* y_b = S_bb x_b = D_bb x_b - D_br D_rr^-1 D_rb x_b (Section 1), with the
+ * inner D_rr^-1 taken by BiCGStab to opts->inner_tol.  xb_dev, yb_dev:
+ * complex128 [n_b][4][3] in label order, not overlapping.  Synchronises the
+ * stream (inner convergence).  Returns GS_MAXITER if the inner solve did not
+ * converge (y_b then uses its last iterate). */
+gs_status schur_apply(gs_ctx* ctx, int type, int dir, int inverse,
+                      const void* xb_dev, void* yb_dev,
+                      const gs_solve_opts* opts, gs_solve_stats* stats);
+
+/* Solve D x = f through the block UL factorisation of Section 1:
+ *   w_b = f_b - D_br D_rr^-1 f_r,   S_bb x_b = w_b (outer GMRES(m) or
+ *   BiCGStab),   x_r = D_rr^-1 (f_r - D_rb x_b).
+ * f_dev, x_dev: complex128 [V][4][3] in site order, not overlapping; x_dev
+ * receives the solution.  stats->true_residual is ||f - D x|| / ||f|| in
+ * FP64.  Synchronises the stream. */
+gs_status schur_solve(gs_ctx* ctx, int type, int dir, int inverse,
+                      const void* f_dev, void* x_dev,
+                      const gs_solve_opts* opts, gs_solve_stats* stats);
+
+/* Text of the last error on this context ("" if none).  The pointer stays
+ * valid until the next call on the context. */
+const char* gs_last_error(const gs_ctx* ctx);
+
+/* Library version string. */
+const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSCHUR_H */

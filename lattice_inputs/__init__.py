@@ -312,3 +312,62 @@ def point_sources(dims, site=0) -> np.ndarray:
     for k in range(12):
         out[k, site, k // 3, k % 3] = 1.0
     return out
+
+
+# ---------------------------------------------------------------------------
+# on-disk cache for the slow generators (a convenience; never required)
+# ---------------------------------------------------------------------------
+
+def _cache_path(name):
+    import os
+    root = os.environ.get("GSCHUR_FIELD_CACHE")
+    if root is None:
+        root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            ".cache", "fields")
+    return os.path.join(root, name + ".npy")
+
+
+def cached(name, make):
+    """Load ``name`` from the field cache, else build it with ``make()`` and store it."""
+    import os
+    path = _cache_path(name)
+    if os.path.exists(path):
+        try:
+            return np.load(path)
+        except (OSError, ValueError):
+            pass
+    arr = make()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp%d.npy" % os.getpid()
+        np.save(tmp, arr)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return arr
+
+
+def workload_gauge(name):
+    """The seeded gauge field of one of the named workloads.
+
+    * ``"4^4 eps0.3"``            : 4^4, exp(i 0.3 H), seed 0
+    * ``"8^4 heatbath b5.4"``     : 8^4, plaquette action beta = 5.4,
+                                    200 Cabibbo-Marinari sweeps, cold start, seed 1
+    * ``"16^3x32 eps0.25 ape5"``  : 16^3 x 32, exp(i 0.25 H) seed 2, 5 APE steps alpha 0.5
+    * ``"24^3x48 eps0.2"``        : 24^3 x 48, exp(i 0.2 H), seed 3
+    * ``"16^4 eps0.2"``           : 16^4, exp(i 0.2 H), seed 4
+    * ``"32^3x64 eps0.2 ape10"``  : 32^3 x 64, exp(i 0.2 H) seed 5, 10 APE steps alpha 0.5
+    """
+    table = {
+        "4^4 eps0.3": ((4, 4, 4, 4), lambda d: random_gauge(d, 0.3, 0)),
+        "8^4 heatbath b5.4": ((8, 8, 8, 8), lambda d: heatbath_gauge(d, 5.4, 200, 1)),
+        "16^3x32 eps0.25 ape5": ((16, 16, 16, 32),
+                                 lambda d: ape_smear(random_gauge(d, 0.25, 2), d, 0.5, 5)),
+        "24^3x48 eps0.2": ((24, 24, 24, 48), lambda d: random_gauge(d, 0.2, 3)),
+        "16^4 eps0.2": ((16, 16, 16, 16), lambda d: random_gauge(d, 0.2, 4)),
+        "32^3x64 eps0.2 ape10": ((32, 32, 32, 64),
+                                 lambda d: ape_smear(random_gauge(d, 0.2, 5), d, 0.5, 10)),
+    }
+    dims, make = table[name]
+    key = name.replace("^", "p").replace(" ", "_")
+    return dims, cached(key, lambda: make(dims))

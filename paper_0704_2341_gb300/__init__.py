@@ -1,0 +1,17 @@
+"""GB300 (sm_103a) library for the gauged renormalisation-group step of
+lattice Wilson fermions: the Schur complement S_bb = D_bb - D_br D_rr^-1 D_rb
+under the Type I / Type II site permutations and their inverses.
+
+The compute path is the CUDA library ``libgschur.so`` (C ABI in
+``include/gschur.h``); this package is its ctypes binding.  PyTorch is used by
+callers only for device memory and streams.
+"""
+from ._binding import *  # noqa: F401,F403
+from ._binding import (Context, GschurError, EXPORTS, LIB_PATH, gs_default_opts,  # noqa: F401
+                       gs_solve_opts, gs_solve_stats, lib)
+
+__all__ = ["Context", "GschurError", "gs_create", "gs_destroy", "gs_set_gauge",
+           "gs_default_opts", "wilson_apply", "permute_sites", "gs_get_permutation",
+           "schur_apply", "schur_solve", "gs_last_error", "gs_version",
+           "GS_TYPE_I", "GS_TYPE_II", "GS_F64", "GS_F32", "GS_BF16", "GS_GMRES",
+           "GS_BICGSTAB", "GS_OK", "GS_MAXITER"]

@@ -1,0 +1,217 @@
+"""ctypes binding of the gschur C ABI (include/gschur.h).
+
+Argument marshalling only: every function here forwards to the entry point of
+the same name in ``libgschur.so``; tensors are turned into device pointers,
+options into the C structs.  There is no fallback: if the library is missing
+the import fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgschur.so")
+
+GS_OK, GS_EINVAL, GS_ENOMEM, GS_MAXITER, GS_BREAKDOWN, GS_NONFINITE, GS_TIMEOUT, \
+    GS_ECUDA, GS_ENOGAUGE = range(9)
+STATUS_NAMES = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOMEM", 3: "GS_MAXITER",
+                4: "GS_BREAKDOWN", 5: "GS_NONFINITE", 6: "GS_TIMEOUT", 7: "GS_ECUDA",
+                8: "GS_ENOGAUGE"}
+GS_TYPE_I, GS_TYPE_II = 1, 2
+GS_F64, GS_F32, GS_BF16 = 0, 1, 2
+GS_GMRES, GS_BICGSTAB = 0, 1
+
+# every symbol the header declares
+EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson_apply",
+           "permute_sites", "gs_get_permutation", "schur_apply", "schur_solve",
+           "gs_last_error", "gs_version")
+
+
+class gs_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("restart", ctypes.c_int), ("outer_solver", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("inner_max_iter", ctypes.c_int),
+                ("inner_prec", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class gs_solve_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("inner_solves", ctypes.c_int), ("inner_iters", ctypes.c_longlong),
+                ("inner_max_seen", ctypes.c_int), ("outer_residual", ctypes.c_double),
+                ("true_residual", ctypes.c_double), ("inner_residual", ctypes.c_double),
+                ("stencil_sites", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            "libgschur.so is not built (expected at %s); run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` first" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64p = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "gs_create": (i32, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.c_double, vp]),
+        "gs_destroy": (i32, [vp]),
+        "gs_set_gauge": (i32, [vp, vp]),
+        "gs_default_opts": (None, [ctypes.POINTER(gs_solve_opts)]),
+        "wilson_apply": (i32, [vp, vp, vp]),
+        "permute_sites": (i32, [vp, i32, i32, i32, i32, vp, vp, i64p]),
+        "gs_get_permutation": (i32, [vp, i32, i32, i32, vp, i64p]),
+        "schur_apply": (i32, [vp, i32, i32, i32, vp, vp, ctypes.POINTER(gs_solve_opts),
+                              ctypes.POINTER(gs_solve_stats)]),
+        "schur_solve": (i32, [vp, i32, i32, i32, vp, vp, ctypes.POINTER(gs_solve_opts),
+                              ctypes.POINTER(gs_solve_stats)]),
+        "gs_last_error": (ctypes.c_char_p, [vp]),
+        "gs_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class GschurError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(t):
+    """Device pointer of a tensor (checked: CUDA, contiguous) or an int."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _check(ctx, status, allow=(GS_OK,)):
+    if status not in allow:
+        raise GschurError(status, gs_last_error(ctx))
+    return status
+
+
+def gs_version():
+    return lib.gs_version().decode()
+
+
+def gs_last_error(ctx):
+    return lib.gs_last_error(ctx).decode()
+
+
+def gs_default_opts(**overrides):
+    o = gs_solve_opts()
+    lib.gs_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def gs_create(dims, m0, stream=None):
+    """Returns the opaque context handle (an int).  stream: a cudaStream_t as int or None."""
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(L) for L in dims])
+    st = lib.gs_create(ctypes.byref(h), d, float(m0), stream)
+    if st != GS_OK:
+        raise GschurError(st, "gs_create failed")
+    return h.value
+
+
+def gs_destroy(ctx):
+    return lib.gs_destroy(ctx)
+
+
+def gs_set_gauge(ctx, U):
+    return _check(ctx, lib.gs_set_gauge(ctx, _ptr(U)))
+
+
+def wilson_apply(ctx, x, y):
+    return _check(ctx, lib.wilson_apply(ctx, _ptr(x), _ptr(y)))
+
+
+def permute_sites(ctx, ptype, dir, inverse, transpose, x, y):
+    nb = ctypes.c_int64()
+    _check(ctx, lib.permute_sites(ctx, ptype, dir, int(bool(inverse)), int(bool(transpose)),
+                                  _ptr(x), _ptr(y), ctypes.byref(nb)))
+    return nb.value
+
+
+def gs_get_permutation(ctx, ptype, dir, inverse, perm):
+    nb = ctypes.c_int64()
+    _check(ctx, lib.gs_get_permutation(ctx, ptype, dir, int(bool(inverse)), _ptr(perm),
+                                       ctypes.byref(nb)))
+    return nb.value
+
+
+def schur_apply(ctx, ptype, dir, inverse, xb, yb, opts=None, allow=(GS_OK,)):
+    o = opts if opts is not None else gs_default_opts()
+    st = gs_solve_stats()
+    _check(ctx, lib.schur_apply(ctx, ptype, dir, int(bool(inverse)), _ptr(xb), _ptr(yb),
+                                ctypes.byref(o), ctypes.byref(st)), allow)
+    return st
+
+
+def schur_solve(ctx, ptype, dir, inverse, f, x, opts=None, allow=(GS_OK,)):
+    o = opts if opts is not None else gs_default_opts()
+    st = gs_solve_stats()
+    _check(ctx, lib.schur_solve(ctx, ptype, dir, int(bool(inverse)), _ptr(f), _ptr(x),
+                                ctypes.byref(o), ctypes.byref(st)), allow)
+    return st
+
+
+class Context:
+    """Owns one gs_ctx; methods forward to the functions above."""
+
+    def __init__(self, dims, m0, stream=None):
+        self.dims = tuple(int(L) for L in dims)
+        self.m0 = float(m0)
+        self.handle = gs_create(self.dims, self.m0, stream)
+
+    def close(self):
+        if self.handle:
+            gs_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_gauge(self, U):
+        return gs_set_gauge(self.handle, U)
+
+    def wilson_apply(self, x, y):
+        return wilson_apply(self.handle, x, y)
+
+    def permute_sites(self, ptype, dir, inverse, transpose, x, y):
+        return permute_sites(self.handle, ptype, dir, inverse, transpose, x, y)
+
+    def get_permutation(self, ptype, dir, inverse, perm):
+        return gs_get_permutation(self.handle, ptype, dir, inverse, perm)
+
+    def schur_apply(self, ptype, dir, inverse, xb, yb, opts=None, allow=(GS_OK,)):
+        return schur_apply(self.handle, ptype, dir, inverse, xb, yb, opts, allow)
+
+    def schur_solve(self, ptype, dir, inverse, f, x, opts=None, allow=(GS_OK,)):
+        return schur_solve(self.handle, ptype, dir, inverse, f, x, opts, allow)

@@ -1,0 +1,258 @@
+// Internal declarations of the gschur CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gschur.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------------------
+// complex double helpers (interleaved re, im in a double2)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cmake(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+// a + i*b and a - i*b
+__host__ __device__ __forceinline__ double2 caddi(double2 a, double2 b) { return make_double2(a.x - b.y, a.y + b.x); }
+__host__ __device__ __forceinline__ double2 csubi(double2 a, double2 b) { return make_double2(a.x + b.y, a.y - b.x); }
+__host__ __device__ __forceinline__ double2 cneg(double2 a) { return make_double2(-a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cmuli(double2 a) { return make_double2(-a.y, a.x); }    // i*a
+__host__ __device__ __forceinline__ double2 cmulmi(double2 a) { return make_double2(a.y, -a.x); }   // -i*a
+// acc += a*b with fused multiply-adds
+__host__ __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a)*b
+__host__ __device__ __forceinline__ void ccfma(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+
+constexpr int kNc = 3;
+constexpr int kNs = 4;
+constexpr int kSiteC = 12;   // complex numbers per site spinor
+constexpr int kLinkC = 9;    // complex numbers per SU(3) link
+
+// ---------------------------------------------------------------------------
+// device-side solver state (one per inner solve workspace)
+// ---------------------------------------------------------------------------
+struct BicgState {
+    double2 rho;      // <rhat, r>
+    double2 alpha;
+    double2 omega;
+    double2 beta;
+    double rr;        // ||r||^2
+    double bb;        // ||b||^2
+    double tol2;      // (tol)^2 * ||b||^2
+    int done;         // 1 when converged or failed: kernels become no-ops
+    int status;       // GS_OK / GS_BREAKDOWN / GS_NONFINITE
+    int iter;         // completed iterations
+    int pad;
+    struct BicgPublic* pub;  // host-mapped mirror the host polls (device pointer)
+};
+
+// The part of the solver state the host reads while iterations are queued:
+// written by the last block of the kernels that change it, followed by a
+// system-scope fence, into pinned host memory mapped into the device.
+struct BicgPublic {
+    int done;
+    int status;
+    int iter;
+    int pad;
+    double rr;
+    double bb;
+};
+
+__device__ __forceinline__ void publish(BicgState* st) {
+    BicgPublic* p = st->pub;
+    if (p) {
+        p->rr = st->rr;
+        p->bb = st->bb;
+        p->iter = st->iter;
+        p->status = st->status;
+        __threadfence_system();
+        p->done = st->done;
+        __threadfence_system();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a permutation plan: label order, neighbour table and label-ordered links
+// ---------------------------------------------------------------------------
+struct Plan {
+    int type = 0;          // 0 = identity (site order), GS_TYPE_I, GS_TYPE_II
+    int dir = 0;
+    int inverse = 0;
+    int64_t nb = 0;        // coarse count (labels [0, nb) are b)
+    int32_t* perm = nullptr;     // [V] label -> site
+    int32_t* label = nullptr;    // [V] site -> label
+    int2* nbr = nullptr;         // [V][4] (fwd label, bwd label) per mu, label-indexed
+    double2* links = nullptr;    // [V][4][9] -1/2 U_mu(perm[j]) in label order
+    bool links_ready = false;
+};
+
+// Reduction scratch for one chain of fused reductions.
+struct RedScratch {
+    double* partial = nullptr;     // [kRedScratchDoubles]
+    unsigned int* counter = nullptr;
+};
+constexpr int kMaxRedBlocks = 1024;
+constexpr int kMaxRedVals = 8;
+constexpr int kMaxRestart = 64;
+// covers kMaxRedBlocks * kMaxRedVals and the multi-dot (64 blocks x 65 vectors x 2)
+constexpr int64_t kRedScratchDoubles = 16384;
+
+// Inner-solver workspace (vectors of n_r sites).
+struct InnerWork {
+    int64_t cap_sites = 0;
+    double2 *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
+    double2 *rhs = nullptr, *sol = nullptr;  // right-hand side and solution of S_bb's inner solve
+    BicgState* st = nullptr;       // device
+    BicgPublic* pub_host = nullptr;  // pinned, mapped
+    BicgPublic* pub_dev = nullptr;   // device alias of pub_host
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    RedScratch red;
+};
+
+// Outer-solver workspace (vectors of n_b sites).
+struct OuterWork {
+    int64_t cap_sites = 0;
+    int cap_m = 0;
+    double2* basis = nullptr;   // [(m+1)][nb*12]
+    double2* w = nullptr;
+    double2* xb = nullptr;
+    double2* wb = nullptr;
+    double2* tmp = nullptr;
+    double2* hbuf = nullptr;    // device: h (m+2), h2 (m+2), (||w||^2, 0)
+    double2* hbuf_host = nullptr;  // pinned copy
+    double2* y = nullptr;       // device coefficients (m+1 entries)
+    double2* y_host = nullptr;  // pinned
+    RedScratch red;
+};
+
+}  // namespace gs
+
+struct gs_ctx {
+    int dims[4];
+    int64_t V = 0;
+    double m0 = 0.0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    bool have_gauge = false;
+    double2* U_abi = nullptr;          // private copy of the caller's field, [V][4][9]
+    std::vector<gs::Plan*> plans;      // plans[0] = identity
+    gs::InnerWork inner;
+    gs::OuterWork outer;
+    double2* full_a = nullptr;         // [V][12] label-ordered scratch
+    double2* full_b = nullptr;
+    double2* full_c = nullptr;
+    double* scal_dev = nullptr;        // small device scratch for norms
+    double* scal_host = nullptr;       // pinned
+    gs::RedScratch red;
+    long long launches = 0;
+    long long stencil_sites = 0;
+    std::string err;
+};
+
+namespace gs {
+
+// error helpers --------------------------------------------------------------
+gs_status set_err(gs_ctx* c, gs_status s, const char* fmt, ...);
+#define GS_CUDA(ctx, call)                                                       \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess)                                                   \
+            return gs::set_err((ctx), GS_ECUDA, "%s failed: %s (%s:%d)", #call,  \
+                               cudaGetErrorString(e_), __FILE__, __LINE__);      \
+    } while (0)
+#define GS_CHECK_LAUNCH(ctx) GS_CUDA(ctx, cudaGetLastError())
+
+// lattice / permutation (lattice.cu) ------------------------------------------
+gs_status get_plan(gs_ctx* c, int type, int dir, int inverse, Plan** out);
+gs_status pack_plan_links(gs_ctx* c, Plan* p);
+void free_plan(Plan* p);
+gs_status launch_gather(gs_ctx* c, const int32_t* perm, const double2* x, double2* y, int64_t n);
+gs_status launch_scatter(gs_ctx* c, const int32_t* perm, const double2* x, double2* y, int64_t n);
+
+// stencil (dslash_f64.cu) -------------------------------------------------------
+// out[k] for labels o0+k, k < n_out:
+//   out = [addend] + sign * ( diag * self + sum_hops U' in )
+// where the input vector is split in two label segments: [a0, a1) read from
+// inA + (l - a0)*12 and [a1, b1) read from inB + (l - a1)*12 (b1 == a1: no B).
+// self is the input at the output label when it lies in [a0, b1).
+enum StencilEpi { EPI_NONE = 0, EPI_DOT_RHAT_V = 1, EPI_DOT_TS = 2 };
+struct StencilArgs {
+    double2* out;
+    int64_t o0, n_out;
+    const double2* inA;
+    int64_t a0, a1;
+    const double2* inB;
+    int64_t b1;
+    const double2* addend;   // may be null
+    double diag;             // m0 + 4
+    int negate;              // sign = -1 if set
+    const int2* nbr;         // plan->nbr (device)
+    const double2* links;    // plan->links (device)
+    // epilogue for the fused inner-solver kernels
+    int epi;
+    const double2* epi_vec;  // rhat (EPI_DOT_RHAT_V) or s (EPI_DOT_TS), same indexing as out
+    BicgState* st;
+    RedScratch red;
+};
+gs_status launch_stencil_f64(gs_ctx* c, const StencilArgs& a);
+
+// BLAS-1 and Krylov kernels (blas.cu) ------------------------------------------
+gs_status launch_bicg_init(gs_ctx* c, InnerWork& w, const double2* b, double2* x, int64_t n,
+                           double tol);
+gs_status launch_bicg_s_update(gs_ctx* c, InnerWork& w, double2* x, int64_t n);
+gs_status launch_bicg_xr_update(gs_ctx* c, InnerWork& w, double2* x, int64_t n);
+gs_status launch_bicg_p_update(gs_ctx* c, InnerWork& w, int64_t n);
+// result[k] = <x_k, y> for k < nvec (x_k = X + k*ld), written to dev_out (complex)
+gs_status launch_multidot(gs_ctx* c, RedScratch red, const double2* X, int64_t ld, int nvec,
+                          const double2* y, int64_t n, double2* dev_out, int accumulate);
+// y -= sum_k coef[k] x_k   (coef on the device); or y += if sign > 0
+gs_status launch_multiaxpy(gs_ctx* c, const double2* X, int64_t ld, int nvec, const double2* coef,
+                           double2* y, int64_t n, int sign);
+// dev_out[0] = ||x||^2 (double)
+gs_status launch_norm2(gs_ctx* c, RedScratch red, const double2* x, int64_t n, double* dev_out);
+// y = a*x (a on host)
+gs_status launch_scale_copy(gs_ctx* c, const double2* x, double2* y, int64_t n, double a);
+gs_status launch_axpby(gs_ctx* c, double2 a, const double2* x, double2 b, double2* y, int64_t n);
+
+// solvers (solver.cu) ---------------------------------------------------------
+gs_status ensure_inner(gs_ctx* c, int64_t sites);
+gs_status ensure_outer(gs_ctx* c, int64_t sites, int m);
+// z = D_rr^-1 t for plan p (vectors of n_r = V - nb sites in label order r)
+gs_status inner_solve(gs_ctx* c, const Plan* p, const double2* t, double2* z,
+                      const gs_solve_opts& o, gs_solve_stats& st);
+gs_status schur_apply_internal(gs_ctx* c, const Plan* p, const double2* xb, double2* yb,
+                               const gs_solve_opts& o, gs_solve_stats& st);
+gs_status outer_solve(gs_ctx* c, const Plan* p, const double2* wb, double2* xb,
+                      const gs_solve_opts& o, gs_solve_stats& st);
+
+int grid_for(int64_t n, int block, int max_blocks);
+
+}  // namespace gs

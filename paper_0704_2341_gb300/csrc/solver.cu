@@ -1,0 +1,483 @@
+// Host drivers of the solvers: the inner D_rr^-1 (BiCGStab, device-resident
+// scalars), S_bb applied as D_bb - D_br D_rr^-1 D_rb (Section 1 of the paper),
+// and the outer solve of S_bb x_b = w_b (restarted GMRES(m) or BiCGStab)
+// followed by the back-substitution of the block UL factorisation.
+#include <math.h>
+
+#include <complex>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+using cplx = std::complex<double>;
+
+static gs_status alloc_dev(gs_ctx* c, void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_err(c, GS_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    }
+    return GS_OK;
+}
+
+static gs_status alloc_red(gs_ctx* c, RedScratch& r) {
+    gs_status s = alloc_dev(c, (void**)&r.partial, kRedScratchDoubles * sizeof(double));
+    if (s != GS_OK) return s;
+    s = alloc_dev(c, (void**)&r.counter, sizeof(unsigned int));
+    if (s != GS_OK) return s;
+    GS_CUDA(c, cudaMemsetAsync(r.counter, 0, sizeof(unsigned int), c->stream));
+    return GS_OK;
+}
+
+gs_status ensure_inner(gs_ctx* c, int64_t sites) {
+    InnerWork& w = c->inner;
+    if (w.st == nullptr) {
+        gs_status s = alloc_dev(c, (void**)&w.st, sizeof(BicgState));
+        if (s != GS_OK) return s;
+        if ((s = alloc_red(c, w.red)) != GS_OK) return s;
+        if (cudaHostAlloc((void**)&w.pub_host, sizeof(BicgPublic), cudaHostAllocMapped) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, GS_ENOMEM, "pinned allocation failed");
+        }
+        GS_CUDA(c, cudaHostGetDevicePointer((void**)&w.pub_dev, w.pub_host, 0));
+        memset(w.pub_host, 0, sizeof(BicgPublic));
+        BicgState init;
+        memset(&init, 0, sizeof init);
+        init.pub = w.pub_dev;
+        GS_CUDA(c, cudaMemcpyAsync(w.st, &init, sizeof init, cudaMemcpyHostToDevice, c->stream));
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int k = 0; k < 4; ++k)
+            GS_CUDA(c, cudaEventCreateWithFlags(&w.ev[k], cudaEventDisableTiming));
+    }
+    if (sites > w.cap_sites) {
+        double2** v[8] = {&w.r, &w.rhat, &w.p, &w.v, &w.s, &w.t, &w.rhs, &w.sol};
+        for (auto pp : v) {
+            cudaFree(*pp);
+            *pp = nullptr;
+        }
+        const size_t bytes = (size_t)sites * kSiteC * sizeof(double2);
+        for (auto pp : v) {
+            gs_status s = alloc_dev(c, (void**)pp, bytes);
+            if (s != GS_OK) return s;
+        }
+        w.cap_sites = sites;
+    }
+    return GS_OK;
+}
+
+gs_status ensure_outer(gs_ctx* c, int64_t sites, int m) {
+    OuterWork& w = c->outer;
+    if (w.red.partial == nullptr) {
+        gs_status s = alloc_red(c, w.red);
+        if (s != GS_OK) return s;
+        if ((s = alloc_dev(c, (void**)&w.hbuf, (2 * (kMaxRestart + 2) + 1) * sizeof(double2))) !=
+            GS_OK)
+            return s;
+        if ((s = alloc_dev(c, (void**)&w.y, (kMaxRestart + 1) * sizeof(double2))) != GS_OK)
+            return s;
+        if (cudaHostAlloc((void**)&w.hbuf_host, (2 * (kMaxRestart + 2) + 1) * sizeof(double2), 0) !=
+                cudaSuccess ||
+            cudaHostAlloc((void**)&w.y_host, (kMaxRestart + 1) * sizeof(double2), 0) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, GS_ENOMEM, "pinned allocation failed");
+        }
+    }
+    if (sites > w.cap_sites || m > w.cap_m) {
+        cudaFree(w.basis);
+        cudaFree(w.w);
+        cudaFree(w.tmp);
+        cudaFree(w.wb);
+        w.basis = w.w = w.tmp = w.wb = nullptr;
+        const size_t vb = (size_t)sites * kSiteC * sizeof(double2);
+        gs_status s;
+        if ((s = alloc_dev(c, (void**)&w.basis, vb * (m + 1))) != GS_OK) return s;
+        if ((s = alloc_dev(c, (void**)&w.w, vb)) != GS_OK) return s;
+        if ((s = alloc_dev(c, (void**)&w.tmp, vb * 6)) != GS_OK) return s;
+        if ((s = alloc_dev(c, (void**)&w.wb, vb)) != GS_OK) return s;
+        w.cap_sites = sites;
+        w.cap_m = m;
+    }
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// inner solve: z = D_rr^-1 t
+// ---------------------------------------------------------------------------
+
+static StencilArgs rr_args(gs_ctx* c, const Plan* p, double2* out, const double2* in) {
+    StencilArgs a;
+    memset(&a, 0, sizeof a);
+    a.out = out;
+    a.o0 = p->nb;
+    a.n_out = c->V - p->nb;
+    a.inA = in;
+    a.a0 = p->nb;
+    a.a1 = c->V;
+    a.inB = nullptr;
+    a.b1 = c->V;
+    a.diag = c->m0 + 4.0;
+    a.nbr = p->nbr;
+    a.links = p->links;
+    return a;
+}
+
+gs_status inner_solve(gs_ctx* c, const Plan* p, const double2* t, double2* z,
+                      const gs_solve_opts& o, gs_solve_stats& st) {
+    const int64_t nr = c->V - p->nb;
+    const int64_t n = nr * kSiteC;
+    gs_status s = ensure_inner(c, nr);
+    if (s != GS_OK) return s;
+    InnerWork& w = c->inner;
+    if ((s = launch_bicg_init(c, w, t, z, n, o.inner_tol)) != GS_OK) return s;
+
+    StencilArgs k1 = rr_args(c, p, w.v, w.p);
+    k1.epi = EPI_DOT_RHAT_V;
+    k1.epi_vec = w.rhat;
+    k1.st = w.st;
+    k1.red = w.red;
+    StencilArgs k3 = rr_args(c, p, w.t, w.s);
+    k3.epi = EPI_DOT_TS;
+    k3.epi_vec = w.s;
+    k3.st = w.st;
+    k3.red = w.red;
+
+    // Iterations are queued ahead of the GPU; the host waits on the event of
+    // the iteration `depth` behind and reads the mapped `done` flag, so at most
+    // `depth` no-op iterations are queued after convergence.
+    const int depth = (o.check_every >= 1 && o.check_every <= 4) ? o.check_every : 2;
+    volatile BicgPublic* pub = w.pub_host;
+    int enq = 0;
+    GS_CUDA(c, cudaEventRecord(w.ev[0], c->stream));  // after init
+    GS_CUDA(c, cudaEventSynchronize(w.ev[0]));
+    if (!pub->done) {
+        for (int it = 0; it < o.inner_max_iter; ++it) {
+            if (it >= depth) {
+                GS_CUDA(c, cudaEventSynchronize(w.ev[(it - depth) % 4]));
+                if (pub->done) break;
+            }
+            if ((s = launch_stencil_f64(c, k1)) != GS_OK) return s;
+            if ((s = launch_bicg_s_update(c, w, z, n)) != GS_OK) return s;
+            if ((s = launch_stencil_f64(c, k3)) != GS_OK) return s;
+            if ((s = launch_bicg_xr_update(c, w, z, n)) != GS_OK) return s;
+            if ((s = launch_bicg_p_update(c, w, n)) != GS_OK) return s;
+            GS_CUDA(c, cudaEventRecord(w.ev[it % 4], c->stream));
+            enq = it + 1;
+        }
+        if (enq > 0) GS_CUDA(c, cudaEventSynchronize(w.ev[(enq - 1) % 4]));
+    }
+    const int iters = pub->iter;
+    const double rel = pub->bb > 0.0 ? sqrt(pub->rr / pub->bb) : 0.0;
+    st.inner_solves += 1;
+    st.inner_iters += iters;
+    if (iters > st.inner_max_seen) st.inner_max_seen = iters;
+    if (rel > st.inner_residual) st.inner_residual = rel;
+    if (pub->status != GS_OK)
+        return set_err(c, (gs_status)pub->status,
+                       "inner BiCGStab on D_rr stopped (status %d) after %d iterations",
+                       pub->status, iters);
+    if (!pub->done)
+        return set_err(c, GS_MAXITER, "inner BiCGStab on D_rr reached %d iterations (rel. residual %.3e)",
+                       iters, rel);
+    return GS_OK;
+}
+
+// y_b = S_bb x_b = D_bb x_b - D_br D_rr^-1 D_rb x_b   (Section 1)
+//   t   = -D_rb x_b            (stencil: r outputs from b inputs)
+//   z   =  D_rr^-1 t            (= -D_rr^-1 D_rb x_b)
+//   y_b =  D_bb x_b + D_br z    (stencil: b outputs from [x_b ; z])
+gs_status schur_apply_internal(gs_ctx* c, const Plan* p, const double2* xb, double2* yb,
+                               const gs_solve_opts& o, gs_solve_stats& st) {
+    const int64_t nb = p->nb, V = c->V;
+    gs_status s = ensure_inner(c, V - nb);
+    if (s != GS_OK) return s;
+    double2* t = c->inner.rhs;
+    double2* z = c->inner.sol;
+    StencilArgs a;
+    memset(&a, 0, sizeof a);
+    a.out = t;
+    a.o0 = nb;
+    a.n_out = V - nb;
+    a.inA = xb;
+    a.a0 = 0;
+    a.a1 = nb;
+    a.b1 = nb;
+    a.diag = c->m0 + 4.0;
+    a.negate = 1;
+    a.nbr = p->nbr;
+    a.links = p->links;
+    s = launch_stencil_f64(c, a);
+    if (s != GS_OK) return s;
+    gs_status si = inner_solve(c, p, t, z, o, st);
+    if (si != GS_OK && si != GS_MAXITER) return si;
+    a.out = yb;
+    a.o0 = 0;
+    a.n_out = nb;
+    a.inA = xb;
+    a.a0 = 0;
+    a.a1 = nb;
+    a.inB = z;
+    a.b1 = V;
+    a.negate = 0;
+    if ((s = launch_stencil_f64(c, a)) != GS_OK) return s;
+    return si;
+}
+
+// ---------------------------------------------------------------------------
+// outer solvers on S_bb x_b = w_b (vectors of nb sites)
+// ---------------------------------------------------------------------------
+
+static gs_status read_norm2(gs_ctx* c, RedScratch red, const double2* x, int64_t n, double* out) {
+    gs_status s = launch_norm2(c, red, x, n, c->scal_dev);
+    if (s != GS_OK) return s;
+    GS_CUDA(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    *out = c->scal_host[0];
+    return GS_OK;
+}
+
+// Restarted GMRES(m) (Saad & Schultz 1986) with classical Gram-Schmidt applied
+// twice (CGS2) on the device and Givens rotations on the host.
+static gs_status outer_gmres(gs_ctx* c, const Plan* p, const double2* wb, double2* xb,
+                             const gs_solve_opts& o, gs_solve_stats& st) {
+    const int64_t nbs = p->nb, n = nbs * kSiteC;
+    const int m = o.restart;
+    gs_status s = ensure_outer(c, nbs, m);
+    if (s != GS_OK) return s;
+    OuterWork& W = c->outer;
+    const size_t vbytes = (size_t)n * sizeof(double2);
+    double2* V = W.basis;
+    double bnorm2;
+    if ((s = read_norm2(c, W.red, wb, n, &bnorm2)) != GS_OK) return s;
+    GS_CUDA(c, cudaMemsetAsync(xb, 0, vbytes, c->stream));
+    if (!(bnorm2 > 0.0)) {
+        st.outer_residual = 0.0;
+        return isfinite(bnorm2) ? GS_OK : set_err(c, GS_NONFINITE, "non-finite right-hand side");
+    }
+    const double bnorm = sqrt(bnorm2);
+    const double target = o.tol * bnorm;
+    int total = 0;
+    bool converged = false;
+    bool first = true;
+    gs_status inner_flag = GS_OK;
+    std::vector<cplx> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m);
+    while (true) {
+        // r = w_b - S x_b  (x_b = 0 on the first cycle)
+        double beta2;
+        if (first) {
+            GS_CUDA(c, cudaMemcpyAsync(V, wb, vbytes, cudaMemcpyDeviceToDevice, c->stream));
+            beta2 = bnorm2;
+        } else {
+            s = schur_apply_internal(c, p, xb, W.w, o, st);
+            if (s == GS_MAXITER) inner_flag = s;
+            else if (s != GS_OK) return s;
+            // V0 = w_b - S x_b
+            if ((s = launch_scale_copy(c, wb, V, n, 1.0)) != GS_OK) return s;
+            if ((s = launch_axpby(c, make_double2(-1.0, 0.0), W.w, make_double2(1.0, 0.0), V, n)) !=
+                GS_OK)
+                return s;
+            if ((s = read_norm2(c, W.red, V, n, &beta2)) != GS_OK) return s;
+        }
+        first = false;
+        const double beta = sqrt(beta2);
+        st.outer_residual = beta / bnorm;
+        if (!isfinite(beta)) return set_err(c, GS_NONFINITE, "non-finite outer residual");
+        if (beta <= target) {
+            converged = true;
+            break;
+        }
+        if (total >= o.max_iter) break;
+        if ((s = launch_scale_copy(c, V, V, n, 1.0 / beta)) != GS_OK) return s;
+        std::fill(g.begin(), g.end(), cplx(0.0));
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            double2* Vj = V + (size_t)j * n;
+            double2* Vn = V + (size_t)(j + 1) * n;
+            s = schur_apply_internal(c, p, Vj, W.w, o, st);
+            if (s == GS_MAXITER) inner_flag = s;
+            else if (s != GS_OK) return s;
+            // CGS2: h = V^H w ; w -= V h ; h2 = V^H w ; w -= V h2
+            double2* h = W.hbuf;
+            double2* h2 = W.hbuf + (m + 2);
+            if ((s = launch_multidot(c, W.red, V, n, j + 1, W.w, n, h, 0)) != GS_OK) return s;
+            if ((s = launch_multiaxpy(c, V, n, j + 1, h, W.w, n, -1)) != GS_OK) return s;
+            if ((s = launch_multidot(c, W.red, V, n, j + 1, W.w, n, h2, 0)) != GS_OK) return s;
+            if ((s = launch_multiaxpy(c, V, n, j + 1, h2, W.w, n, -1)) != GS_OK) return s;
+            if ((s = launch_norm2(c, W.red, W.w, n, (double*)(W.hbuf + 2 * (m + 2)))) != GS_OK)
+                return s;
+            GS_CUDA(c, cudaMemcpyAsync(W.hbuf_host, W.hbuf, (2 * (m + 2) + 1) * sizeof(double2),
+                                       cudaMemcpyDeviceToHost, c->stream));
+            GS_CUDA(c, cudaStreamSynchronize(c->stream));
+            const double hn = sqrt(W.hbuf_host[2 * (m + 2)].x);
+            if (!isfinite(hn)) return set_err(c, GS_NONFINITE, "non-finite Arnoldi norm");
+            for (int i = 0; i <= j; ++i)
+                H[(size_t)i * m + j] = cplx(W.hbuf_host[i].x + W.hbuf_host[m + 2 + i].x,
+                                            W.hbuf_host[i].y + W.hbuf_host[m + 2 + i].y);
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0.0)
+                if ((s = launch_scale_copy(c, W.w, Vn, n, 1.0 / hn)) != GS_OK) return s;
+            // previous rotations, then a new one: G = [[conj(c), conj(s)], [-s, c]]
+            for (int i = 0; i < j; ++i) {
+                const cplx hi = H[(size_t)i * m + j], hi1 = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = std::conj(cs[i]) * hi + std::conj(sn[i]) * hi1;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * hi + cs[i] * hi1;
+            }
+            const cplx aa = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+            const double hh = sqrt(std::norm(aa) + std::norm(bb));
+            if (hh > 0.0) {
+                cs[j] = aa / hh;
+                sn[j] = bb / hh;
+            } else {
+                cs[j] = 1.0;
+                sn[j] = 0.0;
+            }
+            H[(size_t)j * m + j] = hh;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = std::conj(cs[j]) * g[j];
+            ++total;
+            k = j + 1;
+            st.outer_iters = total;
+            st.outer_residual = std::abs(g[j + 1]) / bnorm;
+            if (std::abs(g[j + 1]) <= target || hn == 0.0 || total >= o.max_iter) break;
+        }
+        // y = R^-1 g ; x_b += V y
+        std::vector<cplx> y(k);
+        for (int i = k - 1; i >= 0; --i) {
+            cplx acc = g[i];
+            for (int l = i + 1; l < k; ++l) acc -= H[(size_t)i * m + l] * y[l];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        for (int i = 0; i < k; ++i) W.y_host[i] = make_double2(y[i].real(), y[i].imag());
+        GS_CUDA(c, cudaMemcpyAsync(W.y, W.y_host, k * sizeof(double2), cudaMemcpyHostToDevice,
+                                   c->stream));
+        if ((s = launch_multiaxpy(c, V, n, k, W.y, xb, n, +1)) != GS_OK) return s;
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));  // y_host is reused
+        if (st.outer_residual * bnorm <= target) {
+            converged = true;
+            break;
+        }
+        if (total >= o.max_iter) break;
+    }
+    st.outer_iters = total;
+    if (!converged)
+        return set_err(c, GS_MAXITER, "outer GMRES(%d) reached %d steps (residual %.3e)", m, total,
+                       st.outer_residual);
+    return inner_flag;
+}
+
+// BiCGStab on S_bb (the paper's outer solver, Section 4), host scalars.
+static gs_status outer_bicgstab(gs_ctx* c, const Plan* p, const double2* wb, double2* xb,
+                                const gs_solve_opts& o, gs_solve_stats& st) {
+    const int64_t nbs = p->nb, n = nbs * kSiteC;
+    gs_status s = ensure_outer(c, nbs, o.restart);
+    if (s != GS_OK) return s;
+    OuterWork& W = c->outer;
+    const size_t vbytes = (size_t)n * sizeof(double2);
+    double2 *r = W.tmp, *rhat = W.tmp + n, *pp = W.tmp + 2 * n, *v = W.tmp + 3 * n,
+            *sv = W.tmp + 4 * n, *t = W.tmp + 5 * n;
+    double bnorm2;
+    if ((s = read_norm2(c, W.red, wb, n, &bnorm2)) != GS_OK) return s;
+    GS_CUDA(c, cudaMemsetAsync(xb, 0, vbytes, c->stream));
+    if (!(bnorm2 > 0.0)) {
+        st.outer_residual = 0.0;
+        return isfinite(bnorm2) ? GS_OK : set_err(c, GS_NONFINITE, "non-finite right-hand side");
+    }
+    const double target2 = o.tol * o.tol * bnorm2;
+    GS_CUDA(c, cudaMemcpyAsync(r, wb, vbytes, cudaMemcpyDeviceToDevice, c->stream));
+    GS_CUDA(c, cudaMemcpyAsync(rhat, wb, vbytes, cudaMemcpyDeviceToDevice, c->stream));
+    GS_CUDA(c, cudaMemsetAsync(pp, 0, vbytes, c->stream));
+    GS_CUDA(c, cudaMemsetAsync(v, 0, vbytes, c->stream));
+    auto dot = [&](const double2* a, const double2* b, cplx* out) -> gs_status {
+        gs_status e = launch_multidot(c, W.red, a, n, 1, b, n, W.hbuf, 0);
+        if (e != GS_OK) return e;
+        GS_CUDA(c, cudaMemcpyAsync(W.hbuf_host, W.hbuf, sizeof(double2), cudaMemcpyDeviceToHost,
+                                   c->stream));
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        *out = cplx(W.hbuf_host[0].x, W.hbuf_host[0].y);
+        return GS_OK;
+    };
+    cplx rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    double rr = bnorm2;
+    gs_status inner_flag = GS_OK;
+    bool converged = false;
+    int it = 0;
+    while (it < o.max_iter) {
+        cplx rho;
+        if ((s = dot(rhat, r, &rho)) != GS_OK) return s;
+        if (rho == 0.0) return set_err(c, GS_BREAKDOWN, "outer BiCGStab breakdown (rho = 0)");
+        const cplx beta = (rho / rho_old) * (alpha / omega);
+        // p = r + beta (p - omega v)
+        if ((s = launch_axpby(c, make_double2(-omega.real(), -omega.imag()), v,
+                              make_double2(1.0, 0.0), pp, n)) != GS_OK)
+            return s;
+        if ((s = launch_axpby(c, make_double2(1.0, 0.0), r, make_double2(beta.real(), beta.imag()),
+                              pp, n)) != GS_OK)
+            return s;
+        s = schur_apply_internal(c, p, pp, v, o, st);
+        if (s == GS_MAXITER) inner_flag = s;
+        else if (s != GS_OK) return s;
+        cplx rv;
+        if ((s = dot(rhat, v, &rv)) != GS_OK) return s;
+        alpha = rho / rv;
+        // s = r - alpha v ; x += alpha p
+        GS_CUDA(c, cudaMemcpyAsync(sv, r, vbytes, cudaMemcpyDeviceToDevice, c->stream));
+        if ((s = launch_axpby(c, make_double2(-alpha.real(), -alpha.imag()), v,
+                              make_double2(1.0, 0.0), sv, n)) != GS_OK)
+            return s;
+        if ((s = launch_axpby(c, make_double2(alpha.real(), alpha.imag()), pp,
+                              make_double2(1.0, 0.0), xb, n)) != GS_OK)
+            return s;
+        double ss;
+        if ((s = read_norm2(c, W.red, sv, n, &ss)) != GS_OK) return s;
+        ++it;
+        if (ss <= target2) {
+            rr = ss;
+            converged = true;
+            break;
+        }
+        s = schur_apply_internal(c, p, sv, t, o, st);
+        if (s == GS_MAXITER) inner_flag = s;
+        else if (s != GS_OK) return s;
+        cplx ts, tt;
+        if ((s = dot(t, sv, &ts)) != GS_OK) return s;
+        if ((s = dot(t, t, &tt)) != GS_OK) return s;
+        omega = tt.real() > 0.0 ? ts / tt.real() : 0.0;
+        // x += omega s ; r = s - omega t
+        if ((s = launch_axpby(c, make_double2(omega.real(), omega.imag()), sv,
+                              make_double2(1.0, 0.0), xb, n)) != GS_OK)
+            return s;
+        GS_CUDA(c, cudaMemcpyAsync(r, sv, vbytes, cudaMemcpyDeviceToDevice, c->stream));
+        if ((s = launch_axpby(c, make_double2(-omega.real(), -omega.imag()), t,
+                              make_double2(1.0, 0.0), r, n)) != GS_OK)
+            return s;
+        if ((s = read_norm2(c, W.red, r, n, &rr)) != GS_OK) return s;
+        st.outer_residual = sqrt(rr / bnorm2);
+        if (!isfinite(rr)) return set_err(c, GS_NONFINITE, "non-finite outer residual");
+        if (rr <= target2) {
+            converged = true;
+            break;
+        }
+        if (omega == 0.0) return set_err(c, GS_BREAKDOWN, "outer BiCGStab breakdown (omega = 0)");
+        rho_old = rho;
+    }
+    st.outer_iters = it;
+    st.outer_residual = sqrt(rr / bnorm2);
+    if (!converged)
+        return set_err(c, GS_MAXITER, "outer BiCGStab reached %d steps (residual %.3e)", it,
+                       st.outer_residual);
+    return inner_flag;
+}
+
+gs_status outer_solve(gs_ctx* c, const Plan* p, const double2* wb, double2* xb,
+                      const gs_solve_opts& o, gs_solve_stats& st) {
+    if (o.outer_solver == GS_BICGSTAB) return outer_bicgstab(c, p, wb, xb, o, st);
+    return outer_gmres(c, p, wb, xb, o, st);
+}
+
+}  // namespace gs

@@ -1,0 +1,53 @@
+"""CPU checks of the C ABI: the library loads and exports every declared symbol;
+the product package does not reach the oracle and the oracle does not reach
+the product package."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gschur.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(\w+)\s*\([^;{]*\)\s*;", src)
+    return sorted(set(n for n in names if n not in ("if", "while", "for", "sizeof")))
+
+
+def test_library_exports_every_declared_symbol():
+    import __graft_entry__ as g
+    g.build()
+    import paper_0704_2341_gb300 as gs
+    lib = ctypes.CDLL(gs.LIB_PATH)
+    decl = _declared()
+    assert len(decl) >= 11
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert set(decl) == set(gs.EXPORTS)
+    assert gs.gs_version().startswith("gschur")
+
+
+def test_calls_without_gpu_fail_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_0704_2341_gb300 as gs
+    with pytest.raises(gs.GschurError):
+        gs.gs_create((4, 4, 4, 4), 0.1)
+    o = gs.gs_default_opts()
+    assert o.tol == 1e-10 and o.restart == 30 and o.inner_tol == 1e-12
+
+
+def test_oracle_and_product_are_independent():
+    for dirpath, _, files in os.walk(os.path.join(ROOT, "paper_0704_2341_gb300")):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\boracle\b\s*(import|\.)|from\s+oracle|import\s+oracle", txt), f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            txt = open(os.path.join(ROOT, "oracle", f)).read()
+            assert not re.search(r"(from|import)\s+paper_0704_2341_gb300|libgschur", txt), f

@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (FP64 throughout): the stencil and the permutations differ from the
+oracle only by rounding order (<= 1e-13 relative; indices bit-exact); every
+result that goes through an inner Krylov solve is compared at a tolerance set
+by that solve's stopping criterion.
+"""
+import numpy as np
+import pytest
+
+import lattice_inputs as li
+from oracle import dirac, permute, schur
+from tests.gpu_util import lib, rel, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+TYPES = [(1, 0, False), (2, 0, False), (1, 0, True), (2, 0, True)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = torch_cuda()
+    gs = lib()
+    return torch, gs
+
+
+def _ctx(gs, torch, dims, m0, U):
+    ctx = gs.Context(dims, m0, torch.cuda.current_stream().cuda_stream)
+    ctx.set_gauge(to_dev(U, torch))
+    return ctx
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 8, 8, 8), (6, 4, 2, 8), (2, 2, 2, 2),
+                                  (16, 16, 16, 32)])
+def test_permutation_bit_exact(env, dims):
+    torch, gs = env
+    ctx = gs.Context(dims, 0.0, torch.cuda.current_stream().cuda_stream)
+    V = li.volume(dims)
+    out = torch.empty(V, dtype=torch.int32, device="cuda:0")
+    cases = [(1, 0, inv) for inv in (0, 1)] + [(2, mu, inv) for mu in range(4) for inv in (0, 1)]
+    for t, mu, inv in cases:
+        nb = ctx.get_permutation(t, mu, inv, out)
+        ref, nb_ref = permute.permutation(dims, t, mu, bool(inv))
+        assert nb == nb_ref
+        assert np.array_equal(out.cpu().numpy().astype(np.int64), ref), (t, mu, inv)
+    ctx.close()
+
+
+def test_permute_sites_gather_scatter_bit_exact(env):
+    torch, gs = env
+    dims = (6, 4, 2, 8)
+    V = li.volume(dims)
+    ctx = gs.Context(dims, 0.0, torch.cuda.current_stream().cuda_stream)
+    x = li.gaussian_source(dims, 7)
+    xd = to_dev(x, torch)
+    y = torch.empty_like(xd)
+    z = torch.empty_like(xd)
+    for t, mu, inv in [(1, 0, 0), (1, 0, 1), (2, 1, 0), (2, 3, 1)]:
+        perm, nb = permute.permutation(dims, t, mu, bool(inv))
+        assert ctx.permute_sites(t, mu, inv, 0, xd, y) == nb
+        assert np.array_equal(y.cpu().numpy(), x[perm])          # (P x)_i = x_{p(i)}
+        ctx.permute_sites(t, mu, inv, 1, y, z)
+        assert np.array_equal(z.cpu().numpy(), x)                 # P^T P = 1
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,eps,m0", [((4, 4, 4, 4), 0.3, 0.2), ((2, 2, 2, 2), 0.5, -0.3),
+                                         ((3, 4, 2, 5), 0.4, 0.1), ((6, 4, 4, 8), 0.3, -0.4),
+                                         ((8, 8, 8, 8), 0.2, -0.38)])
+def test_wilson_apply_matches_oracle(env, dims, eps, m0):
+    torch, gs = env
+    U = li.random_gauge(dims, eps, 1)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    x = li.gaussian_source(dims, 3)
+    xd = to_dev(x, torch)
+    yd = torch.empty_like(xd)
+    ctx.wilson_apply(xd, yd)
+    torch.cuda.synchronize()
+    ref = (dirac.wilson_matrix(U, dims, m0) @ x.ravel()).reshape(x.shape)
+    got = yd.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("t,mu,inv", TYPES + [(2, 3, False), (2, 1, True)])
+def test_schur_apply_matches_oracle_4x4(env, t, mu, inv):
+    """4^4, exp(i 0.3 H) seed 0, m0 = 0.2, Gaussian source seed 100 (the small
+    workload), inner tolerance 1e-14: S_bb x_b within 1e-12 of the oracle
+    (direct sparse LU for D_rr^-1)."""
+    torch, gs = env
+    dims, m0 = (4, 4, 4, 4), 0.2
+    U = li.random_gauge(dims, 0.3, 0)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    perm, nb = permute.permutation(dims, t, mu, inv)
+    src = li.gaussian_source(dims, 100).reshape(-1, 12)
+    xb = src[perm[:nb]].ravel()
+    xbd = to_dev(xb, torch)
+    ybd = torch.empty_like(xbd)
+    st = ctx.schur_apply(t, mu, int(inv), xbd, ybd, gs.gs_default_opts(inner_tol=1e-14))
+    D = dirac.wilson_matrix(U, dims, m0)
+    ref = schur.SchurOperator(D, perm, nb, inner="direct")(xb)
+    assert rel(ybd.cpu().numpy(), ref) <= 1e-12
+    assert st.inner_solves == 1 and st.inner_iters > 0
+    ctx.close()
+
+
+def test_schur_columns_match_dense_S(env):
+    """Column probes of S_bb (unit vectors) against the oracle's dense S_bb."""
+    torch, gs = env
+    dims, m0 = (4, 4, 2, 2), 0.3
+    U = li.random_gauge(dims, 0.3, 5)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    for t, mu, inv in [(1, 0, False), (2, 1, True)]:
+        perm, nb = permute.permutation(dims, t, mu, inv)
+        S = schur.schur_dense(dirac.wilson_matrix(U, dims, m0), perm, nb)
+        n = 12 * nb
+        for k in [0, 5, n // 2, n - 1]:
+            e = np.zeros(n, complex)
+            e[k] = 1.0
+            ed = to_dev(e, torch)
+            yd = torch.empty_like(ed)
+            ctx.schur_apply(t, mu, int(inv), ed, yd, gs.gs_default_opts(inner_tol=1e-14))
+            assert rel(yd.cpu().numpy(), S[:, k]) <= 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("t,mu,inv", TYPES)
+def test_schur_solve_matches_direct_solve_4x4(env, t, mu, inv):
+    import scipy.sparse.linalg as sla
+    torch, gs = env
+    dims, m0 = (4, 4, 4, 4), 0.2
+    U = li.random_gauge(dims, 0.3, 0)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    f = li.gaussian_source(dims, 100)
+    fd = to_dev(f, torch)
+    xd = torch.empty_like(fd)
+    st = ctx.schur_solve(t, mu, int(inv), fd, xd, gs.gs_default_opts(tol=1e-11, inner_tol=1e-13))
+    D = dirac.wilson_matrix(U, dims, m0)
+    x = xd.cpu().numpy().ravel()
+    xs = sla.spsolve(D.tocsc(), f.ravel())
+    assert np.linalg.norm(f.ravel() - D @ x) <= 1e-10 * np.linalg.norm(f)
+    assert rel(x, xs) <= 1e-9
+    assert st.true_residual <= 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("outer", ["gmres", "bicgstab"])
+def test_schur_solve_outer_solvers_ragged_lattice(env, outer):
+    """V = 2*2*6*2 = 48 sites (not a multiple of the 32-site tile), n_b = 3."""
+    import scipy.sparse.linalg as sla
+    torch, gs = env
+    dims, m0 = (2, 2, 6, 2), 0.1
+    U = li.random_gauge(dims, 0.4, 9)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    f = li.gaussian_source(dims, 11)
+    fd = to_dev(f, torch)
+    xd = torch.empty_like(fd)
+    solver = gs.GS_GMRES if outer == "gmres" else gs.GS_BICGSTAB
+    for t, mu, inv in TYPES:
+        st = ctx.schur_solve(t, mu, int(inv), fd, xd,
+                             gs.gs_default_opts(outer_solver=solver, inner_tol=1e-13))
+        D = dirac.wilson_matrix(U, dims, m0)
+        xs = sla.spsolve(D.tocsc(), f.ravel())
+        assert rel(xd.cpu().numpy(), xs) <= 1e-9
+        assert st.true_residual <= 1e-10
+    ctx.close()
+
+
+def test_zero_source_and_errors(env):
+    torch, gs = env
+    dims = (4, 4, 2, 2)
+    U = li.random_gauge(dims, 0.3, 2)
+    ctx = gs.Context(dims, 0.1, torch.cuda.current_stream().cuda_stream)
+    z = torch.zeros(li.volume(dims) * 12, dtype=torch.complex128, device="cuda:0")
+    x = torch.full_like(z, 3.0)
+    with pytest.raises(gs.GschurError) as e:
+        ctx.schur_solve(1, 0, 0, z, x)
+    assert e.value.status == gs._binding.GS_ENOGAUGE
+    ctx.set_gauge(to_dev(U, torch))
+    st = ctx.schur_solve(1, 0, 0, z, x)
+    assert st.status == 0 and torch.count_nonzero(x).item() == 0
+    with pytest.raises(gs.GschurError) as e:
+        ctx.schur_solve(3, 0, 0, z, x)
+    assert e.value.status == gs._binding.GS_EINVAL
+    with pytest.raises(gs.GschurError):
+        ctx.schur_solve(2, 4, 0, z, x)
+    f = to_dev(li.gaussian_source(dims, 1), torch)
+    st = ctx.schur_solve(1, 0, 0, f, x, gs.gs_default_opts(inner_max_iter=1),
+                         allow=(gs.GS_OK, gs.GS_MAXITER))
+    assert st.status == gs.GS_MAXITER
+    ctx.close()
+    odd = gs.Context((3, 4, 4, 4), 0.1, torch.cuda.current_stream().cuda_stream)
+    with pytest.raises(gs.GschurError):
+        odd.get_permutation(1, 0, 0, torch.empty(192, dtype=torch.int32, device="cuda:0"))
+    odd.close()
+
+
+_CFG1 = {}
+
+
+def _cfg1_field():
+    if not _CFG1:
+        dims, U = li.workload_gauge("8^4 heatbath b5.4")
+        _CFG1["dims"], _CFG1["U"] = dims, U
+        _CFG1["D"] = dirac.wilson_matrix(U, dims, -0.4)
+    return _CFG1["dims"], _CFG1["U"], _CFG1["D"]
+
+
+@pytest.mark.parametrize("t,mu,inv", TYPES)
+def test_schur_solve_8x4_heatbath_residual(env, t, mu, inv):
+    """The benchmark workload: 8^4 plaquette-action field at beta = 5.4,
+    m0 = -0.4, GMRES(30) to 1e-10 with back-substitution.  The GPU solution
+    must solve the oracle's own D: ||f - D x|| / ||f|| <= 1e-10."""
+    torch, gs = env
+    dims, U, D = _cfg1_field()
+    ctx = _ctx(gs, torch, dims, -0.4, U)
+    f = li.gaussian_source(dims, 100)
+    fd = to_dev(f, torch)
+    xd = torch.empty_like(fd)
+    st = ctx.schur_solve(t, mu, int(inv), fd, xd)
+    x = xd.cpu().numpy().ravel()
+    assert np.linalg.norm(f.ravel() - D @ x) <= 1e-10 * np.linalg.norm(f)
+    assert st.true_residual <= 1e-10
+    ctx.close()
+
+
+def test_schur_solve_8x4_matches_oracle_solution(env):
+    """Type I on the benchmark workload against the oracle's own
+    outer GMRES(30) / inner BiCGStab solve (both to 1e-10 / 1e-12)."""
+    torch, gs = env
+    dims, U, D = _cfg1_field()
+    ctx = _ctx(gs, torch, dims, -0.4, U)
+    f = li.gaussian_source(dims, 100)
+    fd = to_dev(f, torch)
+    xd = torch.empty_like(fd)
+    ctx.schur_solve(1, 0, 0, fd, xd)
+    perm, nb = permute.permutation(dims, 1)
+    xo, info = schur.schur_solve(D, perm, nb, f.ravel(), tol=1e-10, inner="bicgstab",
+                                 inner_tol=1e-12)
+    # both residuals <= 1e-10: the solutions agree to kappa(D) * 2e-10
+    assert rel(xd.cpu().numpy(), xo) <= 1e-7
+    ctx.close()
