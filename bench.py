@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of the Schur-complement solve on one GB300 (or N replicas).
+
+A step is the whole hot path on the 8^4 workload: for each of the four site
+permutations P_I, P_II, P_I^T, P_II^T (Type II along x0), solve D x = f
+through S_bb = D_bb - D_br D_rr^-1 D_rb -- inner BiCGStab on D_rr to 1e-12,
+outer GMRES(30) on S_bb to 1e-10, back-substitution, and the FP64 true
+residual ||f - D x|| / ||f||.  Field: SU(3) plaquette action at beta = 5.4
+(200 Cabibbo-Marinari sweeps from a cold start, seed 1), Wilson m0 = -0.4,
+one complex Gaussian source (seed 100).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (see the design doc for its sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("S_bb solve time to 1e-10 rel. residual (learned+mixed vs plain FP64); "
+          "dslash GB/s vs HBM peak")
+UNIT = "S_bb solves/s"
+WORKLOAD = ("8^4 SU(3) plaquette action beta=5.4 (200 Cabibbo-Marinari sweeps, cold start, "
+            "seed 1), Wilson m0=-0.4 r=1, FP64, P_I/P_II/P_I^T/P_II^T (Type II along x0), "
+            "outer GMRES(30) to 1e-10, inner BiCGStab to 1e-12, back-substitution, "
+            "one Gaussian source (seed 100)")
+PERMS = [(1, 0, 0), (2, 0, 0), (1, 0, 1), (2, 0, 1)]
+FIELD = "8^4 heatbath b5.4"
+M0 = -0.4
+# FP64 peak: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM (the part's nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+NCU_SUMMARY = os.path.join(ROOT, "profiles", "dslash_f64_8x4_traffic.txt")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_0704_2341_gb300", "csrc", "dslash_f64.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic_per_launch():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None if absent or taken on a different kernel source."""
+    try:
+        kv = {}
+        for line in open(NCU_SUMMARY):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha") != _kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%s.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _cpu_sample_main():
+    """Subprocess: the oracle as it stands on one permutation of the workload."""
+    import numpy as np
+    import lattice_inputs as li
+    from oracle import dirac, permute, schur
+    which = int(os.environ.get("GSCHUR_SAMPLE_PERM", "0"))
+    t, mu, inv = PERMS[which]
+    dims, U = li.workload_gauge(FIELD)
+    D = dirac.wilson_matrix(U, dims, M0)
+    f = li.gaussian_source(dims, 100).ravel()
+    perm, nb = permute.permutation(dims, t, mu, bool(inv))
+    t0 = time.perf_counter()
+    x, info = schur.schur_solve(D, perm, nb, f, tol=1e-10, m=30, inner="bicgstab",
+                                inner_tol=1e-12)
+    dt = time.perf_counter() - t0
+    res = float(np.linalg.norm(f - D @ x) / np.linalg.norm(f))
+    print(json.dumps({"seconds": dt, "true_residual": res, "outer_iters": info["iters"],
+                      "inner_iters": int(sum(info["inner_iters"]))}))
+
+
+def cpu_baseline(which=0):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["GSCHUR_SAMPLE_PERM"] = str(which)
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--_cpu-sample"],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("cpu sample failed: " + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    t, mu, inv = PERMS[which]
+    name = ["P_I", "P_II", "P_I^T", "P_II^T"][which]
+    return {"value": 1.0 / out["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one complete %s solve of the 8^4 workload (1 of the 4 solves of a step), "
+                      "numpy/scipy FP64 oracle, 1 thread, %.1f s, true residual %.1e"
+                      % (name, out["seconds"], out["true_residual"])}
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle timed as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import lattice_inputs as li
+    from oracle import dirac, permute, schur
+    dims, U = li.workload_gauge(FIELD)
+    D = dirac.wilson_matrix(U, dims, M0)
+    f = li.gaussian_source(dims, 100).ravel()
+    perm, nb = permute.permutation(dims, 1)
+    # warm-up steps: one S_bb apply each (same code path, bounded)
+    S = schur.SchurOperator(D, perm, nb, inner="bicgstab", inner_tol=1e-12)
+    bi = permute.expand_sites(perm[:nb])
+    for _ in range(args.warmup):
+        S(f[bi])
+    times = []
+    res = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        x, _ = schur.schur_solve(D, perm, nb, f, tol=1e-10, m=30, inner="bicgstab",
+                                 inner_tol=1e-12)
+        times.append(time.perf_counter() - t0)
+        res.append(float(np.linalg.norm(f - D @ x) / np.linalg.norm(f)))
+    tot = sum(times)
+    value = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "solves_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each timed step = one complete P_I solve of the 8^4 "
+                                       "workload by the numpy/scipy FP64 oracle (1 of the 4 "
+                                       "solves of a GPU step); warm-up steps = one S_bb apply; "
+                                       "max true residual %.1e" % max(res)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def kernel_case(args):
+    """One kernel on a large lattice: `reps` launches timed with CUDA events."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_0704_2341_gb300 as gs
+    import lattice_inputs as li
+    dims = tuple(int(v) for v in args.dims.split(","))
+    V = li.volume(dims)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gs.Context(dims, M0, stream.cuda_stream)
+    # unitary links from a cheap recipe (the timing does not depend on the values)
+    U = torch.from_numpy(li.random_gauge((dims[0], dims[1], dims[2], 2), 0.2, 3)).to(dev)
+    U = U.reshape(dims[0] * dims[1] * dims[2], 2, 4, 3, 3)
+    U = U.repeat(1, dims[3] // 2, 1, 1, 1).permute(1, 0, 2, 3, 4).reshape(V, 4, 3, 3).contiguous()
+    ctx.set_gauge(U)
+    x = torch.randn(V, 4, 3, dtype=torch.complex128, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        ctx.wilson_apply(x, y)
+    ctx.profile(True)
+    for _ in range(args.reps):
+        ctx.wilson_apply(x, y)
+    p = ctx.profile_read()
+    ctx.profile(False)
+    ms = p.ms / p.launches
+    peaks = _peaks()
+    out = {"case": args.case, "dims": dims, "sites": V, "launches": p.launches,
+           "us_per_launch": 1e3 * ms, "sites_per_s": V / (ms / 1e3),
+           "tflops": p.flops / p.launches / (ms / 1e3) / 1e12,
+           "frac_fp64_peak": p.flops / p.launches / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+           "gbs": p.bytes / p.launches / (ms / 1e3) / 1e9,
+           "frac_hbm": (p.bytes / p.launches / (ms / 1e3) / 1e9 / peaks["hbm_gbs"])
+           if peaks.get("hbm_gbs") else None,
+           "algorithmic_bytes_per_launch": p.bytes / p.launches}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--_cpu-sample", action="store_true", dest="cpu_sample")
+    ap.add_argument("--case", default=None, choices=["wilson_f64"],
+                    help="kernel micro-benchmark instead of the solve (for profiling)")
+    ap.add_argument("--dims", default="24,24,24,48")
+    ap.add_argument("--reps", type=int, default=20)
+    args = ap.parse_args()
+    if args.cpu_sample:
+        _cpu_sample_main()
+        return
+    if args.case:
+        kernel_case(args)
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_0704_2341_gb300 as gs
+    import lattice_inputs as li
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    dims, U = li.workload_gauge(FIELD)
+    f_np = li.gaussian_source(dims, 100)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gs.Context(dims, M0, stream.cuda_stream)
+    ctx.set_gauge(torch.from_numpy(U).to(dev))
+    f = torch.from_numpy(f_np).to(dev)
+    x = torch.empty_like(f)
+    opts = gs.gs_default_opts()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step():
+        launches = 0
+        worst = 0.0
+        for (t, mu, inv) in PERMS:
+            st = ctx.schur_solve(t, mu, inv, f, x, opts)
+            launches += st.kernel_launches
+            worst = max(worst, st.true_residual)
+        return launches, worst
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(K, profile=False):
+        if profile:
+            ctx.profile(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        launches, worst = 0, 0.0
+        barrier()
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            n, w = step()
+            ev[k][1].record(stream)
+            launches += n
+            worst = max(worst, w)
+        barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        prof = ctx.profile_read() if profile else None
+        if profile:
+            ctx.profile(False)
+        return ms, launches, worst, prof
+
+    smi_index = (os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local]
+                 if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local))
+    clocks = ClockSampler(smi_index)
+    clocks.start()
+    ms, launches, worst, _ = timed(args.steps)
+    clock_info = clocks.stop()
+    # the same K steps again with the stencil launches bracketed by events
+    ms_prof, _, _, prof = timed(args.steps, profile=True)
+
+    # end to end: pinned host source in, four solutions out, every step
+    f_host = torch.from_numpy(f_np).pin_memory()
+    x_host = [torch.empty_like(f_host).pin_memory() for _ in PERMS]
+    e2e_ms = 0.0
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f.copy_(f_host, non_blocking=True)
+        for k, (t, mu, inv) in enumerate(PERMS):
+            ctx.schur_solve(t, mu, inv, f, x, opts)
+            x_host[k].copy_(x, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    barrier()
+
+    if dist is not None:
+        tt = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(tt[0]), float(tt[1])
+
+    solves = len(PERMS) * args.steps * world
+    value = solves / (ms / 1e3)
+    e2e_value = solves / (e2e_ms / 1e3)
+    if rank != 0:
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    avg_ms = prof.ms / max(prof.launches, 1)
+    flops_per_launch = prof.flops / max(prof.launches, 1)
+    bytes_per_launch = prof.bytes / max(prof.launches, 1)
+    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
+    traffic = _ncu_traffic_per_launch()
+    roofline = {
+        "kernel": "k_dslash_f64 (Wilson stencil on label ranges, FP64)",
+        "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+        "peak_source": "FP64 ALU: 152 SMs x 2.07 GHz x 4 flop/clk/SM (nominal 1.25 TFLOP/s; "
+                       "no FP64 entry in MEASURED_PEAKS.json)",
+        "launches": prof.launches, "avg_launch_us": 1e3 * avg_ms,
+        "algorithmic_flops_per_launch": flops_per_launch,
+        "algorithmic_bytes_per_launch": bytes_per_launch,
+        "hbm_view": {"achieved_gbs": bytes_per_launch / (avg_ms / 1e3) / 1e9,
+                     "peak_gbs": peaks.get("hbm_gbs"),
+                     "frac_of_measured": (bytes_per_launch / (avg_ms / 1e3) / 1e9 /
+                                          peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None},
+        "share_of_step": prof.ms / ms_prof if ms_prof > 0 else None,
+        "step_ms_with_events": ms_prof / args.steps,
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "solves_per_step": len(PERMS),
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "max_true_residual": worst},
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": f_host.numel() * f_host.element_size(),
+                "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in x_host)},
+        "clocks": clock_info,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(0)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -155,6 +155,30 @@ gs_status schur_solve(gs_ctx* ctx, int type, int dir, int inverse,
                       const void* f_dev, void* x_dev,
                       const gs_solve_opts* opts, gs_solve_stats* stats);
 
+/* Live timing of the Wilson stencil kernels (the dominant kernels of every
+ * entry point above).  While enabled, each stencil launch is bracketed by two
+ * CUDA events on the context's stream and its algorithmic work is counted:
+ *   hops  = neighbour terms whose input site lies in the launch's input range,
+ *   flops = 168 per hop (spin projection 12, two SU(3) x colour-vector
+ *           products 132, reconstruction 24) + 48 per site with a diagonal
+ *           (m0 + 4) term (FP64 flops, an FMA counting 2),
+ *   bytes = 192 per output site + 192 per input site of the ranges read
+ *           + 144 per link used (hops / 2 when both ends are outputs, else
+ *           one per hop) + 192 per output site of an addend, each datum once.
+ * gs_profile(ctx, 1) resets the counters and starts timing; gs_profile(ctx, 0)
+ * stops it.  gs_profile_read synchronises the stream and returns the totals. */
+typedef struct {
+    long long launches;  /* stencil launches timed */
+    double    ms;        /* summed event-to-event durations of those launches */
+    long long sites;     /* output sites */
+    long long hops;      /* in-range neighbour terms */
+    double    flops;     /* algorithmic flops as defined above */
+    double    bytes;     /* algorithmic bytes as defined above */
+} gs_kernel_profile;
+
+gs_status gs_profile(gs_ctx* ctx, int enable);
+gs_status gs_profile_read(gs_ctx* ctx, gs_kernel_profile* out);
+
 /* Text of the last error on this context ("" if none).  The pointer stays
  * valid until the next call on the context. */
 const char* gs_last_error(const gs_ctx* ctx);

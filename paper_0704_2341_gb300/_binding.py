@@ -25,7 +25,7 @@ GS_GMRES, GS_BICGSTAB = 0, 1
 # every symbol the header declares
 EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson_apply",
            "permute_sites", "gs_get_permutation", "schur_apply", "schur_solve",
-           "gs_last_error", "gs_version")
+           "gs_last_error", "gs_version", "gs_profile", "gs_profile_read")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -41,6 +41,15 @@ class gs_solve_stats(ctypes.Structure):
                 ("inner_max_seen", ctypes.c_int), ("outer_residual", ctypes.c_double),
                 ("true_residual", ctypes.c_double), ("inner_residual", ctypes.c_double),
                 ("stencil_sites", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class gs_kernel_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("sites", ctypes.c_longlong), ("hops", ctypes.c_longlong),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -67,6 +76,8 @@ def _load():
                               ctypes.POINTER(gs_solve_stats)]),
         "gs_last_error": (ctypes.c_char_p, [vp]),
         "gs_version": (ctypes.c_char_p, []),
+        "gs_profile": (i32, [vp, i32]),
+        "gs_profile_read": (i32, [vp, ctypes.POINTER(gs_kernel_profile)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -173,6 +184,16 @@ def schur_solve(ctx, ptype, dir, inverse, f, x, opts=None, allow=(GS_OK,)):
     return st
 
 
+def gs_profile(ctx, enable):
+    return _check(ctx, lib.gs_profile(ctx, int(bool(enable))))
+
+
+def gs_profile_read(ctx):
+    out = gs_kernel_profile()
+    _check(ctx, lib.gs_profile_read(ctx, ctypes.byref(out)))
+    return out
+
+
 class Context:
     """Owns one gs_ctx; methods forward to the functions above."""
 
@@ -215,3 +236,9 @@ class Context:
 
     def schur_solve(self, ptype, dir, inverse, f, x, opts=None, allow=(GS_OK,)):
         return schur_solve(self.handle, ptype, dir, inverse, f, x, opts, allow)
+
+    def profile(self, enable):
+        return gs_profile(self.handle, enable)
+
+    def profile_read(self):
+        return gs_profile_read(self.handle)

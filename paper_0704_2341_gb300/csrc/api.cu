@@ -178,6 +178,7 @@ gs_status wilson_apply(gs_ctx* c, const void* x_dev, void* y_dev) {
     a.a1 = c->V;
     a.b1 = c->V;
     a.diag = c->m0 + 4.0;
+    a.plan = p;
     a.nbr = p->nbr;
     a.links = p->links;
     return launch_stencil_f64(c, a);
@@ -287,7 +288,8 @@ gs_status schur_solve(gs_ctx* c, int type, int dir, int inverse, const void* f_d
         a.diag = c->m0 + 4.0;
         a.negate = 1;
         a.addend = F;
-        a.nbr = p->nbr;
+        a.plan = p;
+    a.nbr = p->nbr;
         a.links = p->links;
         if ((e = launch_stencil_f64(c, a)) != GS_OK) return e;
         // S_bb x_b = w_b, x_b written into the b part of X
@@ -323,6 +325,7 @@ gs_status schur_solve(gs_ctx* c, int type, int dir, int inverse, const void* f_d
         rd.diag = c->m0 + 4.0;
         rd.negate = 1;
         rd.addend = f;
+        rd.plan = id;
         rd.nbr = id->nbr;
         rd.links = id->links;
         if ((e = launch_stencil_f64(c, rd)) != GS_OK) return e;

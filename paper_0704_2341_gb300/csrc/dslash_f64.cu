@@ -155,7 +155,9 @@ __device__ __forceinline__ void hop_mu(const StencilArgs& a, int64_t j, bool val
 
 template <int EPI>
 __global__ void __launch_bounds__(kThreads) k_dslash_f64(StencilArgs a) {
-    if (a.st != nullptr && a.st->done) return;
+    const bool skip = a.st != nullptr && a.st->done;
+    if (a.ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *a.ran = skip ? 0 : 1;
+    if (skip) return;
     __shared__ double red[4][24][kSitesPerBlock];
     __shared__ double bred[4][kMaxRedVals];
     const int warp = threadIdx.x >> 5;
@@ -317,8 +319,17 @@ __global__ void __launch_bounds__(kThreads) k_dslash_f64(StencilArgs a) {
 
 }  // namespace
 
-gs_status launch_stencil_f64(gs_ctx* c, const StencilArgs& a) {
-    if (a.n_out <= 0) return GS_OK;
+gs_status launch_stencil_f64(gs_ctx* c, const StencilArgs& args) {
+    if (args.n_out <= 0) return GS_OK;
+    StencilArgs a = args;
+    int slot = -1;
+    if (c->prof.on) {
+        gs_status s = prof_begin(c, &slot);
+        if (s != GS_OK) return s;
+        a.ran = c->prof.ran_dev + slot;
+    } else {
+        a.ran = nullptr;
+    }
     const int64_t blocks_needed = (a.n_out + kSitesPerBlock - 1) / kSitesPerBlock;
     int max_blocks = (a.epi == EPI_NONE) ? (1 << 30) : kMaxRedBlocks;
     const int g = (int)(blocks_needed < max_blocks ? blocks_needed : max_blocks);
@@ -330,6 +341,7 @@ gs_status launch_stencil_f64(gs_ctx* c, const StencilArgs& a) {
     c->launches++;
     c->stencil_sites += a.n_out;
     GS_CHECK_LAUNCH(c);
+    if (slot >= 0) return prof_end(c, slot, a.plan, a);
     return GS_OK;
 }
 

@@ -112,7 +112,24 @@ struct Plan {
     int2* nbr = nullptr;         // [V][4] (fwd label, bwd label) per mu, label-indexed
     double2* links = nullptr;    // [V][4][9] -1/2 U_mu(perm[j]) in label order
     bool links_ready = false;
+    long long hops[2][2] = {{0, 0}, {0, 0}};  // [out set][in set] in-set neighbour terms (0 = b, 1 = r)
 };
+
+// Event-timed stencil launches (gs_profile).
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;      // 2 per slot
+    struct Pending {
+        int slot;
+        long long sites, hops;
+        double flops, bytes;
+    };
+    std::vector<Pending> pending;
+    int* ran_dev = nullptr;           // per slot: 1 if the launch did work (not an early exit)
+    int* ran_host = nullptr;          // pinned
+    gs_kernel_profile tot{};
+};
+constexpr int kProfSlots = 2048;
 
 // Reduction scratch for one chain of fused reductions.
 struct RedScratch {
@@ -174,6 +191,7 @@ struct gs_ctx {
     gs::RedScratch red;
     long long launches = 0;
     long long stencil_sites = 0;
+    gs::Profiler prof;
     std::string err;
 };
 
@@ -214,6 +232,7 @@ struct StencilArgs {
     const double2* addend;   // may be null
     double diag;             // m0 + 4
     int negate;              // sign = -1 if set
+    const Plan* plan;        // host-side plan (work counting only; never read on the device)
     const int2* nbr;         // plan->nbr (device)
     const double2* links;    // plan->links (device)
     // epilogue for the fused inner-solver kernels
@@ -221,8 +240,15 @@ struct StencilArgs {
     const double2* epi_vec;  // rhat (EPI_DOT_RHAT_V) or s (EPI_DOT_TS), same indexing as out
     BicgState* st;
     RedScratch red;
+    int* ran;                // profiling: set to 1 if the launch did work, 0 if it exited early
 };
 gs_status launch_stencil_f64(gs_ctx* c, const StencilArgs& a);
+// profiling (api.cu): work counted for one stencil launch on plan p
+void stencil_work(const gs_ctx* c, const Plan* p, const StencilArgs& a, long long* hops,
+                  double* flops, double* bytes);
+gs_status prof_begin(gs_ctx* c, int* slot);
+gs_status prof_end(gs_ctx* c, int slot, const Plan* p, const StencilArgs& a);
+gs_status prof_harvest(gs_ctx* c);
 
 // BLAS-1 and Krylov kernels (blas.cu) ------------------------------------------
 gs_status launch_bicg_init(gs_ctx* c, InnerWork& w, const double2* b, double2* x, int64_t n,

@@ -111,6 +111,24 @@ __global__ void k_build_nbr(Dims d, int64_t V, const int32_t* __restrict__ perm,
     }
 }
 
+// hops[o][i] += number of (j, direction) with j in set o and its neighbour in
+// set i (0 = b = labels below nb, 1 = r): the work counter of gs_profile.
+__global__ void k_count_hops(int64_t V, int64_t nb, const int2* __restrict__ nbr,
+                             unsigned long long* __restrict__ hops) {
+    unsigned long long loc[4] = {0, 0, 0, 0};
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < V;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int o = j < nb ? 0 : 1;
+        for (int mu = 0; mu < 4; ++mu) {
+            const int2 n = nbr[j * 4 + mu];
+            loc[o * 2 + (n.x < nb ? 0 : 1)] += 1;
+            loc[o * 2 + (n.y < nb ? 0 : 1)] += 1;
+        }
+    }
+    for (int q = 0; q < 4; ++q)
+        if (loc[q]) atomicAdd(hops + q, loc[q]);
+}
+
 // links[j][mu][k] = -1/2 * U[perm[j]][mu][k]  (the factor is exact in binary)
 __global__ void k_pack_links(int64_t V, const int32_t* __restrict__ perm,
                              const double2* __restrict__ U, double2* __restrict__ links) {
@@ -232,6 +250,26 @@ gs_status get_plan(gs_ctx* c, int type, int dir, int inverse, Plan** out) {
     if (e != cudaSuccess) {
         free_plan(p);
         return set_err(c, GS_ECUDA, "building the permutation plan: %s", cudaGetErrorString(e));
+    }
+    {
+        unsigned long long* dh = nullptr;
+        unsigned long long hh[4] = {0, 0, 0, 0};
+        if (cudaMalloc(&dh, sizeof hh) != cudaSuccess) {
+            cudaGetLastError();
+            free_plan(p);
+            return set_err(c, GS_ENOMEM, "allocating the hop counters failed");
+        }
+        cudaMemsetAsync(dh, 0, sizeof hh, c->stream);
+        k_count_hops<<<g, 256, 0, c->stream>>>(V, p->nb, p->nbr, dh);
+        c->launches++;
+        cudaMemcpyAsync(hh, dh, sizeof hh, cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        cudaFree(dh);
+        if (e2 != cudaSuccess) {
+            free_plan(p);
+            return set_err(c, GS_ECUDA, "counting hops: %s", cudaGetErrorString(e2));
+        }
+        for (int q = 0; q < 4; ++q) p->hops[q / 2][q % 2] = (long long)hh[q];
     }
     c->plans.push_back(p);
     gs_status s = pack_plan_links(c, p);

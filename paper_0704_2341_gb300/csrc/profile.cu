@@ -1,0 +1,119 @@
+// Live timing of the stencil launches (gs_profile / gs_profile_read) and the
+// algorithmic work each launch represents.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+// Which of the two label sets (b = [0, nb), r = [nb, V)) a range covers.
+static void sets_of(int64_t lo, int64_t hi, int64_t nb, int64_t V, bool* has_b, bool* has_r) {
+    *has_b = lo < nb && hi > 0;
+    *has_r = hi > nb && lo < V;
+}
+
+void stencil_work(const gs_ctx* c, const Plan* p, const StencilArgs& a, long long* hops,
+                  double* flops, double* bytes) {
+    const int64_t V = c->V, nb = p->nb;
+    bool ob, orr, ib, ir;
+    sets_of(a.o0, a.o0 + a.n_out, nb, V, &ob, &orr);
+    sets_of(a.a0, a.b1, nb, V, &ib, &ir);
+    const bool out_set[2] = {ob, orr}, in_set[2] = {ib, ir};
+    const int64_t set_size[2] = {nb, V - nb};
+    long long h = 0;
+    double link_uses = 0.0;
+    long long diag_sites = 0;
+    for (int o = 0; o < 2; ++o) {
+        if (!out_set[o]) continue;
+        if (in_set[o]) diag_sites += set_size[o];
+        for (int i = 0; i < 2; ++i) {
+            if (!in_set[i]) continue;
+            h += p->hops[o][i];
+            link_uses += (o == i) ? 0.5 * p->hops[o][i] : (double)p->hops[o][i];
+        }
+    }
+    const int64_t in_sites = a.b1 - a.a0;
+    *hops = h;
+    *flops = 168.0 * h + 48.0 * diag_sites;
+    *bytes = 192.0 * a.n_out + 192.0 * in_sites + 144.0 * link_uses +
+             (a.addend ? 192.0 * a.n_out : 0.0);
+}
+
+gs_status prof_harvest(gs_ctx* c) {
+    Profiler& P = c->prof;
+    if (P.pending.empty()) return GS_OK;
+    GS_CUDA(c, cudaEventSynchronize(P.ev[2 * P.pending.back().slot + 1]));
+    GS_CUDA(c, cudaMemcpy(P.ran_host, P.ran_dev, kProfSlots * sizeof(int), cudaMemcpyDeviceToHost));
+    for (const auto& q : P.pending) {
+        if (!P.ran_host[q.slot]) continue;  // a queued launch that found the solve finished
+        float ms = 0.f;
+        GS_CUDA(c, cudaEventElapsedTime(&ms, P.ev[2 * q.slot], P.ev[2 * q.slot + 1]));
+        P.tot.launches += 1;
+        P.tot.ms += ms;
+        P.tot.sites += q.sites;
+        P.tot.hops += q.hops;
+        P.tot.flops += q.flops;
+        P.tot.bytes += q.bytes;
+    }
+    P.pending.clear();
+    return GS_OK;
+}
+
+gs_status prof_begin(gs_ctx* c, int* slot) {
+    Profiler& P = c->prof;
+    if ((int)P.pending.size() >= kProfSlots) {
+        gs_status s = prof_harvest(c);
+        if (s != GS_OK) return s;
+    }
+    *slot = (int)P.pending.size();
+    GS_CUDA(c, cudaEventRecord(P.ev[2 * *slot], c->stream));
+    return GS_OK;
+}
+
+gs_status prof_end(gs_ctx* c, int slot, const Plan* p, const StencilArgs& a) {
+    Profiler& P = c->prof;
+    GS_CUDA(c, cudaEventRecord(P.ev[2 * slot + 1], c->stream));
+    Profiler::Pending q;
+    q.slot = slot;
+    q.sites = a.n_out;
+    stencil_work(c, p, a, &q.hops, &q.flops, &q.bytes);
+    P.pending.push_back(q);
+    return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+gs_status gs_profile(gs_ctx* c, int enable) {
+    if (!c) return GS_EINVAL;
+    Profiler& P = c->prof;
+    if (enable) {
+        if (P.ev.empty()) {
+            P.ev.resize(2 * kProfSlots);
+            for (auto& e : P.ev) GS_CUDA(c, cudaEventCreate(&e));
+            GS_CUDA(c, cudaMalloc(&P.ran_dev, kProfSlots * sizeof(int)));
+            GS_CUDA(c, cudaHostAlloc(&P.ran_host, kProfSlots * sizeof(int), 0));
+        }
+        gs_status s = prof_harvest(c);
+        if (s != GS_OK) return s;
+        P.tot = gs_kernel_profile{};
+        P.on = true;
+    } else {
+        gs_status s = prof_harvest(c);
+        P.on = false;
+        if (s != GS_OK) return s;
+    }
+    return GS_OK;
+}
+
+gs_status gs_profile_read(gs_ctx* c, gs_kernel_profile* out) {
+    if (!c || !out) return GS_EINVAL;
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    gs_status s = prof_harvest(c);
+    if (s != GS_OK) return s;
+    *out = c->prof.tot;
+    return GS_OK;
+}
+
+}  // extern "C"

@@ -120,6 +120,7 @@ static StencilArgs rr_args(gs_ctx* c, const Plan* p, double2* out, const double2
     a.inB = nullptr;
     a.b1 = c->V;
     a.diag = c->m0 + 4.0;
+    a.plan = p;
     a.nbr = p->nbr;
     a.links = p->links;
     return a;
@@ -207,6 +208,7 @@ gs_status schur_apply_internal(gs_ctx* c, const Plan* p, const double2* xb, doub
     a.b1 = nb;
     a.diag = c->m0 + 4.0;
     a.negate = 1;
+    a.plan = p;
     a.nbr = p->nbr;
     a.links = p->links;
     s = launch_stencil_f64(c, a);
