@@ -64,7 +64,8 @@ typedef enum {
     GS_NONFINITE = 5,  /* NaN or Inf met in a solver scalar */
     GS_TIMEOUT = 6,    /* a bounded device-side wait gave up */
     GS_ECUDA = 7,      /* a CUDA runtime call failed */
-    GS_ENOGAUGE = 8    /* no gauge field set yet */
+    GS_ENOGAUGE = 8,   /* no gauge field set yet */
+    GS_ETOOLARGE = 9   /* lattice larger than wilson_apply_noalloc's static scratch */
 } gs_status;
 
 enum { GS_TYPE_I = 1, GS_TYPE_II = 2 };
@@ -154,6 +155,29 @@ gs_status schur_apply(gs_ctx* ctx, int type, int dir, int inverse,
 gs_status schur_solve(gs_ctx* ctx, int type, int dir, int inverse,
                       const void* f_dev, void* x_dev,
                       const gs_solve_opts* opts, gs_solve_stats* stats);
+
+/* y = D x on the full lattice, like wilson_apply, for callers that cannot
+ * allocate device memory: a service whose device memory is all handed out by
+ * its own pool allocator, or one that cannot afford the device-wide
+ * synchronisation cudaFree implies.  It needs no context and allocates
+ * nothing.  The paper has no counterpart; it is the same operator and the
+ * same stencil kernel as wilson_apply.
+ *
+ * U_dev: complex128 [V][4][3][3] (site order), x_dev, y_dev: complex128
+ * [V][4][3] (site order, not overlapping), all caller-owned device memory;
+ * stream: a cudaStream_t or NULL.  Asynchronous.
+ *
+ * Scratch: the stencil's neighbour table and packed links are written into
+ * one static device array of 4.75 MiB (room for V <= 8192 sites, e.g. 8^4),
+ * which every GPU that loads the library holds until the process exits.
+ * Larger lattices return GS_ETOOLARGE.  Every call overwrites the whole
+ * table it uses, so no state carries over between calls; but all calls on a
+ * device share the one array, so calls whose GPU work overlaps (e.g. on two
+ * streams at once) race.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. */
+gs_status wilson_apply_noalloc(const int dims[4], double m0, const void* U_dev,
+                               const void* x_dev, void* y_dev, void* stream);
 
 /* Live timing of the Wilson stencil kernels (the dominant kernels of every
  * entry point above).  While enabled, each stencil launch is bracketed by two

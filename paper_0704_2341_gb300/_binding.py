@@ -14,10 +14,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgschur.so")
 
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_MAXITER, GS_BREAKDOWN, GS_NONFINITE, GS_TIMEOUT, \
-    GS_ECUDA, GS_ENOGAUGE = range(9)
+    GS_ECUDA, GS_ENOGAUGE, GS_ETOOLARGE = range(10)
 STATUS_NAMES = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOMEM", 3: "GS_MAXITER",
                 4: "GS_BREAKDOWN", 5: "GS_NONFINITE", 6: "GS_TIMEOUT", 7: "GS_ECUDA",
-                8: "GS_ENOGAUGE"}
+                8: "GS_ENOGAUGE", 9: "GS_ETOOLARGE"}
 GS_TYPE_I, GS_TYPE_II = 1, 2
 GS_F64, GS_F32, GS_BF16 = 0, 1, 2
 GS_GMRES, GS_BICGSTAB = 0, 1
@@ -25,7 +25,8 @@ GS_GMRES, GS_BICGSTAB = 0, 1
 # every symbol the header declares
 EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson_apply",
            "permute_sites", "gs_get_permutation", "schur_apply", "schur_solve",
-           "gs_last_error", "gs_version", "gs_profile", "gs_profile_read")
+           "gs_last_error", "gs_version", "gs_profile", "gs_profile_read",
+           "wilson_apply_noalloc")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -77,6 +78,8 @@ def _load():
         "gs_last_error": (ctypes.c_char_p, [vp]),
         "gs_version": (ctypes.c_char_p, []),
         "gs_profile": (i32, [vp, i32]),
+        "wilson_apply_noalloc": (i32, [ctypes.POINTER(ctypes.c_int), ctypes.c_double, vp, vp,
+                                       vp, vp]),
         "gs_profile_read": (i32, [vp, ctypes.POINTER(gs_kernel_profile)]),
     }
     for name, (res, args) in sig.items():
@@ -182,6 +185,12 @@ def schur_solve(ctx, ptype, dir, inverse, f, x, opts=None, allow=(GS_OK,)):
     _check(ctx, lib.schur_solve(ctx, ptype, dir, int(bool(inverse)), _ptr(f), _ptr(x),
                                 ctypes.byref(o), ctypes.byref(st)), allow)
     return st
+
+
+def wilson_apply_noalloc(dims, m0, U, x, y, stream=None):
+    """y = D x without a context and without allocating (returns the status)."""
+    d = (ctypes.c_int * 4)(*[int(L) for L in dims])
+    return lib.wilson_apply_noalloc(d, float(m0), _ptr(U), _ptr(x), _ptr(y), stream)
 
 
 def gs_profile(ctx, enable):

@@ -345,4 +345,17 @@ gs_status launch_stencil_f64(gs_ctx* c, const StencilArgs& args) {
     return GS_OK;
 }
 
+// The same kernel launched on a caller's stream without a context (no
+// profiling, no epilogue): used by the entry point that allocates nothing.
+gs_status launch_stencil_f64_on(const StencilArgs& args, cudaStream_t stream) {
+    if (args.n_out <= 0) return GS_OK;
+    StencilArgs a = args;
+    a.ran = nullptr;
+    a.epi = EPI_NONE;
+    a.st = nullptr;
+    const int64_t g = (a.n_out + kSitesPerBlock - 1) / kSitesPerBlock;
+    k_dslash_f64<EPI_NONE><<<(int)g, kThreads, 0, stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ECUDA;
+}
+
 }  // namespace gs

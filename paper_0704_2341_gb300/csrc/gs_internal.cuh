@@ -243,6 +243,7 @@ struct StencilArgs {
     int* ran;                // profiling: set to 1 if the launch did work, 0 if it exited early
 };
 gs_status launch_stencil_f64(gs_ctx* c, const StencilArgs& a);
+gs_status launch_stencil_f64_on(const StencilArgs& a, cudaStream_t stream);
 // profiling (api.cu): work counted for one stencil launch on plan p
 void stencil_work(const gs_ctx* c, const Plan* p, const StencilArgs& a, long long* hops,
                   double* flops, double* bytes);
