@@ -81,8 +81,13 @@ typedef struct {
     int    outer_solver;   /* GS_GMRES or GS_BICGSTAB [GS_GMRES] */
     double inner_tol;      /* inner: ||t - D_rr z|| / ||t|| for each D_rr^-1 [1e-12] */
     int    inner_max_iter; /* inner: BiCGStab iterations per solve [5000] */
-    int    inner_prec;     /* arithmetic of the inner D_rr solve: GS_F64 [GS_F64] */
-    int    check_every;    /* inner convergence is read back every k iterations [4] */
+    int    inner_prec;     /* inner D_rr solve: GS_F64 (plain BiCGStab), or GS_F32 /
+                            * GS_BF16: FP64 defect correction around a BiCGStab with
+                            * FP32 arithmetic and FP32 / BF16 storage (12-real links);
+                            * the result meets inner_tol in FP64 either way [GS_F64] */
+    int    check_every;    /* inner iterations queued ahead of the convergence read-back, 1..4 [2] */
+    double lowp_tol;       /* relative tolerance of each low-precision solve; 0 = 1e-5
+                            * for GS_F32, 3e-2 for GS_BF16 [0] */
 } gs_solve_opts;
 
 /* Statistics written by schur_apply / schur_solve (may be NULL). */
@@ -97,6 +102,8 @@ typedef struct {
     double    inner_residual;  /* largest final inner relative residual seen */
     long long stencil_sites;   /* output sites of all stencil launches (work counter) */
     long long kernel_launches; /* kernels enqueued by the call */
+    long long lowp_cycles;     /* defect-correction cycles of the mixed inner solves */
+    long long lowp_fallbacks;  /* mixed inner solves finished by the FP64 BiCGStab */
 } gs_solve_stats;
 
 /* Create a context for a dims[0] x dims[1] x dims[2] x dims[3] periodic

@@ -70,22 +70,28 @@ def neighbour(dims, mu, step):
     return site_index(x, dims)
 
 
-def wilson_matrix(U, dims, m0, r=1.0):
+def wilson_matrix(U, dims, m0, r=1.0, rows_of=None):
     """Assembled (12V x 12V) CSR matrix of the Wilson-Dirac operator above.
 
     U: complex128 (V, 4, 3, 3), U[s, mu] the link from s to s + mu-hat.
     Duplicate (row-block, column-block) entries -- the forward and backward
     hop reach the same site when L_mu = 2 -- are summed.
+    rows_of: optional list of sites; then only their block rows are built
+    and the result is (12 len(rows_of) x 12V), row block i = site rows_of[i]
+    (to check large lattices on sampled sites).
     """
     dims = tuple(int(L) for L in dims)
     V = int(np.prod(dims))
     U = np.asarray(U, dtype=np.complex128).reshape(V, 4, 3, 3)
     I4 = np.eye(4)
     rows, cols, vals = [], [], []
-    site = np.arange(V)
+    all_sites = np.arange(V)
+    site = all_sites if rows_of is None else np.asarray(rows_of, dtype=np.int64)
+    nrow = site.size
+    out_row = np.arange(nrow)
 
     def add_blocks(row_sites, col_sites, blocks):
-        # blocks: (V, 12, 12)
+        # blocks: (nrow, 12, 12); row_sites index the output block rows
         rr = 12 * row_sites[:, None, None] + np.arange(12)[None, :, None]
         cc = 12 * col_sites[:, None, None] + np.arange(12)[None, None, :]
         rr, cc = np.broadcast_arrays(rr, cc)
@@ -93,22 +99,22 @@ def wilson_matrix(U, dims, m0, r=1.0):
         cols.append(cc.ravel())
         vals.append(blocks.ravel())
 
-    diag = np.broadcast_to((m0 + 4.0 * r) * np.eye(12), (V, 12, 12))
-    add_blocks(site, site, diag)
+    diag = np.broadcast_to((m0 + 4.0 * r) * np.eye(12), (nrow, 12, 12))
+    add_blocks(out_row, site, diag)
     for mu in range(4):
-        fwd = neighbour(dims, mu, +1)
-        bwd = neighbour(dims, mu, -1)
+        fwd = neighbour(dims, mu, +1)[site]
+        bwd = neighbour(dims, mu, -1)[site]
         Pm = -0.5 * (r * I4 - GAMMA[mu])    # multiplies U_mu(x) psi(x+mu)
         Pp = -0.5 * (r * I4 + GAMMA[mu])    # multiplies U_mu(x-mu)^dag psi(x-mu)
-        Uf = U[:, mu]                                   # U_mu(x)
+        Uf = U[site, mu]                                # U_mu(x)
         Ub = np.conj(np.swapaxes(U[bwd, mu], -1, -2))   # U_mu(x-mu)^dagger
-        Bf = np.einsum("ab,sij->saibj", Pm, Uf).reshape(V, 12, 12)
-        Bb = np.einsum("ab,sij->saibj", Pp, Ub).reshape(V, 12, 12)
-        add_blocks(site, fwd, Bf)
-        add_blocks(site, bwd, Bb)
+        Bf = np.einsum("ab,sij->saibj", Pm, Uf).reshape(nrow, 12, 12)
+        Bb = np.einsum("ab,sij->saibj", Pp, Ub).reshape(nrow, 12, 12)
+        add_blocks(out_row, fwd, Bf)
+        add_blocks(out_row, bwd, Bb)
     rows = np.concatenate(rows)
     cols = np.concatenate(cols)
     vals = np.concatenate(vals)
-    D = sp.coo_matrix((vals, (rows, cols)), shape=(12 * V, 12 * V)).tocsr()
+    D = sp.coo_matrix((vals, (rows, cols)), shape=(12 * nrow, 12 * V)).tocsr()
     D.sum_duplicates()
     return D

@@ -33,7 +33,8 @@ class gs_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("restart", ctypes.c_int), ("outer_solver", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("inner_max_iter", ctypes.c_int),
-                ("inner_prec", ctypes.c_int), ("check_every", ctypes.c_int)]
+                ("inner_prec", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("lowp_tol", ctypes.c_double)]
 
 
 class gs_solve_stats(ctypes.Structure):
@@ -41,7 +42,8 @@ class gs_solve_stats(ctypes.Structure):
                 ("inner_solves", ctypes.c_int), ("inner_iters", ctypes.c_longlong),
                 ("inner_max_seen", ctypes.c_int), ("outer_residual", ctypes.c_double),
                 ("true_residual", ctypes.c_double), ("inner_residual", ctypes.c_double),
-                ("stencil_sites", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong)]
+                ("stencil_sites", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
+                ("lowp_cycles", ctypes.c_longlong), ("lowp_fallbacks", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

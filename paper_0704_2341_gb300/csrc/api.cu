@@ -21,8 +21,10 @@ gs_status check_opts(gs_ctx* c, const gs_solve_opts& o) {
         return set_err(c, GS_EINVAL, "iteration limits must be positive");
     if (o.outer_solver != GS_GMRES && o.outer_solver != GS_BICGSTAB)
         return set_err(c, GS_EINVAL, "unknown outer solver %d", o.outer_solver);
-    if (o.inner_prec != GS_F64)
-        return set_err(c, GS_EINVAL, "inner precision %d is not available", o.inner_prec);
+    if (o.inner_prec != GS_F64 && o.inner_prec != GS_F32 && o.inner_prec != GS_BF16)
+        return set_err(c, GS_EINVAL, "unknown inner precision %d", o.inner_prec);
+    if (!(o.lowp_tol >= 0.0) || o.lowp_tol >= 1.0)
+        return set_err(c, GS_EINVAL, "lowp_tol must be in [0, 1)");
     return GS_OK;
 }
 
@@ -50,6 +52,7 @@ void gs_default_opts(gs_solve_opts* o) {
     o->inner_max_iter = 5000;
     o->inner_prec = GS_F64;
     o->check_every = 2;
+    o->lowp_tol = 0.0;
 }
 
 const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -108,6 +111,7 @@ gs_status gs_destroy(gs_ctx* c) {
     if (!c) return GS_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    free_mixed(c);
     for (Plan* p : c->plans) free_plan(p);
     c->plans.clear();
     cudaFree(c->U_abi);
@@ -156,6 +160,7 @@ gs_status gs_set_gauge(gs_ctx* c, const void* U_dev) {
     GS_CUDA(c, cudaMemcpyAsync(c->U_abi, U_dev, (size_t)c->V * 36 * sizeof(double2),
                                cudaMemcpyDeviceToDevice, c->stream));
     c->have_gauge = true;
+    invalidate_mixed_links(c);
     for (Plan* p : c->plans) {
         gs_status s = pack_plan_links(c, p);
         if (s != GS_OK) return s;

@@ -192,6 +192,7 @@ struct gs_ctx {
     long long launches = 0;
     long long stencil_sites = 0;
     gs::Profiler prof;
+    void* mixed = nullptr;             // mixed-precision state (mixed.cu)
     std::string err;
 };
 
@@ -272,9 +273,16 @@ gs_status launch_axpby(gs_ctx* c, double2 a, const double2* x, double2 b, double
 // solvers (solver.cu) ---------------------------------------------------------
 gs_status ensure_inner(gs_ctx* c, int64_t sites);
 gs_status ensure_outer(gs_ctx* c, int64_t sites, int m);
-// z = D_rr^-1 t for plan p (vectors of n_r = V - nb sites in label order r)
+// z = D_rr^-1 t for plan p (vectors of n_r = V - nb sites in label order r),
+// dispatched on o.inner_prec to the FP64 BiCGStab or the mixed solve.
 gs_status inner_solve(gs_ctx* c, const Plan* p, const double2* t, double2* z,
                       const gs_solve_opts& o, gs_solve_stats& st);
+gs_status inner_solve_f64(gs_ctx* c, const Plan* p, const double2* t, double2* z,
+                          const gs_solve_opts& o, gs_solve_stats& st);
+gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2* z,
+                            const gs_solve_opts& o, gs_solve_stats& st);
+void free_mixed(gs_ctx* c);
+void invalidate_mixed_links(gs_ctx* c);
 gs_status schur_apply_internal(gs_ctx* c, const Plan* p, const double2* xb, double2* yb,
                                const gs_solve_opts& o, gs_solve_stats& st);
 gs_status outer_solve(gs_ctx* c, const Plan* p, const double2* wb, double2* xb,

@@ -128,6 +128,12 @@ static StencilArgs rr_args(gs_ctx* c, const Plan* p, double2* out, const double2
 
 gs_status inner_solve(gs_ctx* c, const Plan* p, const double2* t, double2* z,
                       const gs_solve_opts& o, gs_solve_stats& st) {
+    if (o.inner_prec == GS_F32 || o.inner_prec == GS_BF16) return inner_solve_mixed(c, p, t, z, o, st);
+    return inner_solve_f64(c, p, t, z, o, st);
+}
+
+gs_status inner_solve_f64(gs_ctx* c, const Plan* p, const double2* t, double2* z,
+                          const gs_solve_opts& o, gs_solve_stats& st) {
     const int64_t nr = c->V - p->nb;
     const int64_t n = nr * kSiteC;
     gs_status s = ensure_inner(c, nr);

@@ -115,3 +115,13 @@ def test_two_site_extent_adds_both_hops():
     s, t = 0, 1  # sites (0,0,0,0) and (1,0,0,0)
     blk = D[12 * s:12 * s + 12, 12 * t:12 * t + 12]
     assert np.allclose(blk, -np.eye(12))
+
+
+def test_sampled_rows_equal_full_matrix_rows():
+    dims = (3, 4, 2, 4)
+    U = li.random_gauge(dims, 0.4, 12)
+    D = dirac.wilson_matrix(U, dims, 0.1)
+    sites = np.array([0, 5, 17, 95])
+    Ds = dirac.wilson_matrix(U, dims, 0.1, rows_of=sites)
+    idx = (12 * sites[:, None] + np.arange(12)[None]).ravel()
+    assert abs(Ds - D[idx]).max() == 0
