@@ -223,16 +223,27 @@ def kernel_case(args):
     ctx.set_gauge(U)
     x = torch.randn(V, 4, 3, dtype=torch.complex128, device=dev)
     y = torch.empty_like(x)
+    if args.case == "wilson_f64":
+        prec = gs.GS_F64
+        run = lambda: ctx.wilson_apply(x, y)   # noqa: E731
+    else:
+        prec = gs.GS_F32 if args.prec == "f32" else gs.GS_BF16
+        xl = torch.empty(gs.lowp_bytes(V, prec), dtype=torch.uint8, device=dev)
+        yl = torch.empty_like(xl)
+        ctx.lowp_pack(0, 0, 0, prec, x, xl)
+        run = lambda: ctx.wilson_apply_lowp(0, 0, 0, prec, xl, yl)   # noqa: E731
+    del U
     for _ in range(3):
-        ctx.wilson_apply(x, y)
+        run()
     ctx.profile(True)
     for _ in range(args.reps):
-        ctx.wilson_apply(x, y)
-    p = ctx.profile_read()
+        run()
+    p = ctx.profile_read(prec)
     ctx.profile(False)
     ms = p.ms / p.launches
     peaks = _peaks()
-    out = {"case": args.case, "dims": dims, "sites": V, "launches": p.launches,
+    out = {"case": args.case, "prec": args.prec if args.case != "wilson_f64" else "f64",
+           "dims": dims, "sites": V, "launches": p.launches,
            "us_per_launch": 1e3 * ms, "sites_per_s": V / (ms / 1e3),
            "tflops": p.flops / p.launches / (ms / 1e3) / 1e12,
            "frac_fp64_peak": p.flops / p.launches / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
@@ -252,8 +263,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--_cpu-sample", action="store_true", dest="cpu_sample")
-    ap.add_argument("--case", default=None, choices=["wilson_f64"],
+    ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp"],
                     help="kernel micro-benchmark instead of the solve (for profiling)")
+    ap.add_argument("--prec", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--dims", default="24,24,24,48")
     ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()

@@ -208,7 +208,31 @@ typedef struct {
 } gs_kernel_profile;
 
 gs_status gs_profile(gs_ctx* ctx, int enable);
-gs_status gs_profile_read(gs_ctx* ctx, gs_kernel_profile* out);
+/* prec selects the stencil family: GS_F64 (k_dslash_f64), GS_F32 or GS_BF16
+ * (the low-precision stencil; bytes use 96 / 48 B per spinor and 48 / 24 B
+ * per 12-real link). */
+gs_status gs_profile_read(gs_ctx* ctx, int prec, gs_kernel_profile* out);
+
+/* Low-precision vectors and stencil: the arithmetic of the mixed inner solve
+ * (GS_F32 / GS_BF16 storage, FP32 arithmetic, links stored as two rows of
+ * -1/2 U with the third row rebuilt as the SU(3) cross product).
+ * Set: type == 0 is the whole lattice in site order (n = V, operator D);
+ * GS_TYPE_I / GS_TYPE_II (with dir, inverse) is the rest set r of that
+ * permutation in label order (n = V - n_b, operator D_rr of Section 1).
+ * A low-precision vector of n sites holds each site's 24 reals
+ * ([spin][colour][re, im]) component-major in 16-byte groups:
+ *   GS_F32 : float  [6][n][4]  (group g holds reals 4g .. 4g+3), n x 96 bytes;
+ *   GS_BF16: bf16   [3][n][8]  (group g holds reals 8g .. 8g+7), n x 48 bytes.
+ * gs_lowp_pack rounds a complex128 [n][4][3] vector to that layout,
+ * gs_lowp_unpack widens it back; wilson_apply_lowp computes y = D x (or
+ * D_rr x) in FP32 arithmetic.  Caller-owned device buffers, not overlapping.
+ * Asynchronous. */
+gs_status gs_lowp_pack(gs_ctx* ctx, int type, int dir, int inverse, int prec,
+                       const void* x_dev, void* x_lp_dev);
+gs_status gs_lowp_unpack(gs_ctx* ctx, int type, int dir, int inverse, int prec,
+                         const void* x_lp_dev, void* x_dev);
+gs_status wilson_apply_lowp(gs_ctx* ctx, int type, int dir, int inverse, int prec,
+                            const void* x_lp_dev, void* y_lp_dev);
 
 /* Text of the last error on this context ("" if none).  The pointer stays
  * valid until the next call on the context. */

@@ -26,7 +26,7 @@ GS_GMRES, GS_BICGSTAB = 0, 1
 EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson_apply",
            "permute_sites", "gs_get_permutation", "schur_apply", "schur_solve",
            "gs_last_error", "gs_version", "gs_profile", "gs_profile_read",
-           "wilson_apply_noalloc")
+           "wilson_apply_noalloc", "gs_lowp_pack", "gs_lowp_unpack", "wilson_apply_lowp")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -82,7 +82,10 @@ def _load():
         "gs_profile": (i32, [vp, i32]),
         "wilson_apply_noalloc": (i32, [ctypes.POINTER(ctypes.c_int), ctypes.c_double, vp, vp,
                                        vp, vp]),
-        "gs_profile_read": (i32, [vp, ctypes.POINTER(gs_kernel_profile)]),
+        "gs_profile_read": (i32, [vp, i32, ctypes.POINTER(gs_kernel_profile)]),
+        "gs_lowp_pack": (i32, [vp, i32, i32, i32, i32, vp, vp]),
+        "gs_lowp_unpack": (i32, [vp, i32, i32, i32, i32, vp, vp]),
+        "wilson_apply_lowp": (i32, [vp, i32, i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -199,10 +202,30 @@ def gs_profile(ctx, enable):
     return _check(ctx, lib.gs_profile(ctx, int(bool(enable))))
 
 
-def gs_profile_read(ctx):
+def gs_profile_read(ctx, prec=GS_F64):
     out = gs_kernel_profile()
-    _check(ctx, lib.gs_profile_read(ctx, ctypes.byref(out)))
+    _check(ctx, lib.gs_profile_read(ctx, prec, ctypes.byref(out)))
     return out
+
+
+def lowp_bytes(n_sites, prec):
+    """Size of a low-precision vector of n sites."""
+    return n_sites * (48 if prec == GS_BF16 else 96)
+
+
+def gs_lowp_pack(ctx, ptype, dir, inverse, prec, x, x_lp):
+    return _check(ctx, lib.gs_lowp_pack(ctx, ptype, dir, int(bool(inverse)), prec, _ptr(x),
+                                        _ptr(x_lp)))
+
+
+def gs_lowp_unpack(ctx, ptype, dir, inverse, prec, x_lp, x):
+    return _check(ctx, lib.gs_lowp_unpack(ctx, ptype, dir, int(bool(inverse)), prec, _ptr(x_lp),
+                                          _ptr(x)))
+
+
+def wilson_apply_lowp(ctx, ptype, dir, inverse, prec, x_lp, y_lp):
+    return _check(ctx, lib.wilson_apply_lowp(ctx, ptype, dir, int(bool(inverse)), prec,
+                                             _ptr(x_lp), _ptr(y_lp)))
 
 
 class Context:
@@ -251,5 +274,14 @@ class Context:
     def profile(self, enable):
         return gs_profile(self.handle, enable)
 
-    def profile_read(self):
-        return gs_profile_read(self.handle)
+    def profile_read(self, prec=GS_F64):
+        return gs_profile_read(self.handle, prec)
+
+    def lowp_pack(self, ptype, dir, inverse, prec, x, x_lp):
+        return gs_lowp_pack(self.handle, ptype, dir, inverse, prec, x, x_lp)
+
+    def lowp_unpack(self, ptype, dir, inverse, prec, x_lp, x):
+        return gs_lowp_unpack(self.handle, ptype, dir, inverse, prec, x_lp, x)
+
+    def wilson_apply_lowp(self, ptype, dir, inverse, prec, x_lp, y_lp):
+        return wilson_apply_lowp(self.handle, ptype, dir, inverse, prec, x_lp, y_lp)

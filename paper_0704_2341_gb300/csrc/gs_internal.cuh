@@ -121,13 +121,14 @@ struct Profiler {
     std::vector<cudaEvent_t> ev;      // 2 per slot
     struct Pending {
         int slot;
+        int prec;                     // GS_F64 / GS_F32 / GS_BF16 stencil
         long long sites, hops;
         double flops, bytes;
     };
     std::vector<Pending> pending;
     int* ran_dev = nullptr;           // per slot: 1 if the launch did work (not an early exit)
     int* ran_host = nullptr;          // pinned
-    gs_kernel_profile tot{};
+    gs_kernel_profile tot[3] = {};    // by stencil precision
 };
 constexpr int kProfSlots = 2048;
 
@@ -250,6 +251,8 @@ void stencil_work(const gs_ctx* c, const Plan* p, const StencilArgs& a, long lon
                   double* flops, double* bytes);
 gs_status prof_begin(gs_ctx* c, int* slot);
 gs_status prof_end(gs_ctx* c, int slot, const Plan* p, const StencilArgs& a);
+gs_status prof_end_work(gs_ctx* c, int slot, int prec, long long sites, long long hops,
+                        double flops, double bytes);
 gs_status prof_harvest(gs_ctx* c);
 
 // BLAS-1 and Krylov kernels (blas.cu) ------------------------------------------

@@ -656,6 +656,33 @@ __global__ void k_lp_accum(const void* e, const double* __restrict__ rr64, doubl
     }
 }
 
+// complex128 AoS (n sites) <-> low-precision SoA
+template <class S>
+__global__ void k_lp_pack(const double2* __restrict__ x, void* y, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        float f[24];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            const double2 v = x[k * 12 + q];
+            f[2 * q] = (float)v.x;
+            f[2 * q + 1] = (float)v.y;
+        }
+        Store<S>::store_spinor(y, n, k, f);
+    }
+}
+
+template <class S>
+__global__ void k_lp_unpack(const void* x, double2* __restrict__ y, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        float f[24];
+        Store<S>::load_spinor(x, n, k, f);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) y[k * 12 + q] = make_double2((double)f[2 * q], (double)f[2 * q + 1]);
+    }
+}
+
 // compact rest-set neighbour table and low-precision links from a plan
 template <class S>
 __global__ void k_lp_tables(int64_t nb, int64_t n, const int2* __restrict__ nbr,
@@ -686,8 +713,18 @@ int lp_block(int64_t n, int sms) {
     return 32;
 }
 
+// Launch the low-precision stencil; with profiling on, bracket it by events
+// and count its algorithmic work (168 flop per in-set hop + 48 per site;
+// bytes: spinor in + out, one link read per link used, each datum once).
 template <class S>
-gs_status launch_lp_stencil(gs_ctx* c, LpArgs a, int slot_ok, long long* launches) {
+gs_status launch_lp_stencil(gs_ctx* c, LpArgs a, long long hops, long long* launches) {
+    int slot = -1;
+    a.ran = nullptr;
+    if (c->prof.on) {
+        gs_status s = prof_begin(c, &slot);
+        if (s != GS_OK) return s;
+        a.ran = c->prof.ran_dev + slot;
+    }
     const int b = lp_block(a.n, c->num_sms);
     int64_t g = (a.n + b - 1) / b;
     if (a.epi != EPI_NONE && g > kMaxRedBlocks) g = kMaxRedBlocks;
@@ -696,9 +733,14 @@ gs_status launch_lp_stencil(gs_ctx* c, LpArgs a, int slot_ok, long long* launche
         case EPI_DOT_RHAT_V: k_dslash_lp<S, EPI_DOT_RHAT_V><<<(int)g, b, 0, c->stream>>>(a); break;
         default: k_dslash_lp<S, EPI_DOT_TS><<<(int)g, b, 0, c->stream>>>(a); break;
     }
-    (void)slot_ok;
     ++*launches;
     GS_CHECK_LAUNCH(c);
+    if (slot >= 0) {
+        const double sb = (double)Store<S>::spinor_bytes, lb = (double)Store<S>::link_bytes;
+        const int prec = sizeof(S) == 4 ? GS_F32 : GS_BF16;
+        return prof_end_work(c, slot, prec, a.n, hops, 168.0 * hops + 48.0 * a.n,
+                             2.0 * sb * a.n + lb * 0.5 * hops);
+    }
     return GS_OK;
 }
 
@@ -723,7 +765,9 @@ struct LpWork {
 struct LpPlanData {
     const Plan* plan = nullptr;
     int prec = -1;
-    const double2* links_src = nullptr;
+    int64_t nb = 0;        // labels below nb are excluded (0 for the full lattice)
+    int64_t n = 0;         // sites of the set
+    long long hops = 0;    // in-set neighbour terms of one D application
     int2* nbr_r = nullptr;
     void* links = nullptr;
 };
@@ -811,7 +855,11 @@ static gs_status lp_plan(gs_ctx* c, const Plan* p, int prec, LpPlanData** out) {
     LpPlanData pd;
     pd.plan = p;
     pd.prec = prec;
-    const int64_t n = c->V - p->nb;
+    // the identity plan stands for the whole lattice; a permutation for its rest set
+    pd.nb = (p->type == 0) ? 0 : p->nb;
+    pd.n = c->V - pd.nb;
+    pd.hops = (p->type == 0) ? p->hops[0][0] : p->hops[1][1];
+    const int64_t n = pd.n;
     if (cudaMalloc(&pd.nbr_r, (size_t)n * 4 * sizeof(int2)) != cudaSuccess ||
         cudaMalloc(&pd.links, (size_t)n * 4 * link_bytes(prec)) != cudaSuccess) {
         cudaGetLastError();
@@ -819,10 +867,10 @@ static gs_status lp_plan(gs_ctx* c, const Plan* p, int prec, LpPlanData** out) {
     }
     const int g = grid_for(n, 256, c->num_sms * 8);
     if (prec == GS_BF16)
-        k_lp_tables<__nv_bfloat16><<<g, 256, 0, c->stream>>>(p->nb, n, p->nbr, p->links, pd.nbr_r,
+        k_lp_tables<__nv_bfloat16><<<g, 256, 0, c->stream>>>(pd.nb, n, p->nbr, p->links, pd.nbr_r,
                                                              pd.links);
     else
-        k_lp_tables<float><<<g, 256, 0, c->stream>>>(p->nb, n, p->nbr, p->links, pd.nbr_r, pd.links);
+        k_lp_tables<float><<<g, 256, 0, c->stream>>>(pd.nb, n, p->nbr, p->links, pd.nbr_r, pd.links);
     c->launches++;
     GS_CHECK_LAUNCH(c);
     m->plans.push_back(pd);
@@ -879,10 +927,10 @@ static gs_status lp_bicgstab(gs_ctx* c, LpPlanData* pd, int64_t n, float tol, in
                 GS_CUDA(c, cudaEventSynchronize(iw.ev[(it - depth) % 4]));
                 if (pub->done) break;
             }
-            if ((s = launch_lp_stencil<S>(c, k1, 1, &dummy)) != GS_OK) return s;
+            if ((s = launch_lp_stencil<S>(c, k1, pd->hops, &dummy)) != GS_OK) return s;
             k_lp_s<S><<<gr, bb, 0, c->stream>>>(w.r, w.v, w.p, w.s, w.x, n, w.st, w.partial,
                                                  w.counter);
-            if ((s = launch_lp_stencil<S>(c, k3, 1, &dummy)) != GS_OK) return s;
+            if ((s = launch_lp_stencil<S>(c, k3, pd->hops, &dummy)) != GS_OK) return s;
             k_lp_xr<S><<<gr, bb, 0, c->stream>>>(w.s, w.t, w.rhat, w.x, w.r, n, w.st, w.partial,
                                                   w.counter);
             k_lp_p<S><<<gp, bb, 0, c->stream>>>(w.r, w.v, w.p, n, w.st);
@@ -1018,4 +1066,81 @@ gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2*
     return GS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// ABI: low-precision vectors and the low-precision stencil
+// ---------------------------------------------------------------------------
+static gs_status lp_entry(gs_ctx* c, int type, int dir, int inverse, int prec, LpPlanData** pd) {
+    if (!c) return GS_EINVAL;
+    if (prec != GS_F32 && prec != GS_BF16)
+        return set_err(c, GS_EINVAL, "low-precision calls take GS_F32 or GS_BF16, not %d", prec);
+    if (type != 0 && type != GS_TYPE_I && type != GS_TYPE_II)
+        return set_err(c, GS_EINVAL, "unknown permutation type %d", type);
+    if (!c->have_gauge) return set_err(c, GS_ENOGAUGE, "no gauge field set");
+    Plan* p = nullptr;
+    gs_status s = get_plan(c, type, dir, inverse, &p);
+    if (s != GS_OK) return s;
+    return lp_plan(c, p, prec, pd);
+}
+
 }  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+gs_status gs_lowp_pack(gs_ctx* c, int type, int dir, int inverse, int prec, const void* x_dev,
+                       void* x_lp_dev) {
+    LpPlanData* pd = nullptr;
+    gs_status s = lp_entry(c, type, dir, inverse, prec, &pd);
+    if (s != GS_OK) return s;
+    if (!x_dev || !x_lp_dev) return set_err(c, GS_EINVAL, "null vector");
+    const int g = grid_for(pd->n, 256, c->num_sms * 8);
+    if (prec == GS_BF16)
+        k_lp_pack<__nv_bfloat16><<<g, 256, 0, c->stream>>>((const double2*)x_dev, x_lp_dev, pd->n);
+    else
+        k_lp_pack<float><<<g, 256, 0, c->stream>>>((const double2*)x_dev, x_lp_dev, pd->n);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+gs_status gs_lowp_unpack(gs_ctx* c, int type, int dir, int inverse, int prec,
+                         const void* x_lp_dev, void* x_dev) {
+    LpPlanData* pd = nullptr;
+    gs_status s = lp_entry(c, type, dir, inverse, prec, &pd);
+    if (s != GS_OK) return s;
+    if (!x_dev || !x_lp_dev) return set_err(c, GS_EINVAL, "null vector");
+    const int g = grid_for(pd->n, 256, c->num_sms * 8);
+    if (prec == GS_BF16)
+        k_lp_unpack<__nv_bfloat16><<<g, 256, 0, c->stream>>>(x_lp_dev, (double2*)x_dev, pd->n);
+    else
+        k_lp_unpack<float><<<g, 256, 0, c->stream>>>(x_lp_dev, (double2*)x_dev, pd->n);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+gs_status wilson_apply_lowp(gs_ctx* c, int type, int dir, int inverse, int prec,
+                            const void* x_lp_dev, void* y_lp_dev) {
+    LpPlanData* pd = nullptr;
+    gs_status s = lp_entry(c, type, dir, inverse, prec, &pd);
+    if (s != GS_OK) return s;
+    if (!x_lp_dev || !y_lp_dev) return set_err(c, GS_EINVAL, "null vector");
+    LpArgs a;
+    memset(&a, 0, sizeof a);
+    a.out = y_lp_dev;
+    a.in = x_lp_dev;
+    a.links = pd->links;
+    a.nbr = pd->nbr_r;
+    a.n = pd->n;
+    a.diag = (float)(c->m0 + 4.0);
+    a.epi = EPI_NONE;
+    long long launches = 0;
+    s = (prec == GS_BF16) ? launch_lp_stencil<__nv_bfloat16>(c, a, pd->hops, &launches)
+                          : launch_lp_stencil<float>(c, a, pd->hops, &launches);
+    c->launches += launches;
+    c->stencil_sites += pd->n;
+    return s;
+}
+
+}  // extern "C"

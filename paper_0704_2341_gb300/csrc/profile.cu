@@ -46,12 +46,13 @@ gs_status prof_harvest(gs_ctx* c) {
         if (!P.ran_host[q.slot]) continue;  // a queued launch that found the solve finished
         float ms = 0.f;
         GS_CUDA(c, cudaEventElapsedTime(&ms, P.ev[2 * q.slot], P.ev[2 * q.slot + 1]));
-        P.tot.launches += 1;
-        P.tot.ms += ms;
-        P.tot.sites += q.sites;
-        P.tot.hops += q.hops;
-        P.tot.flops += q.flops;
-        P.tot.bytes += q.bytes;
+        gs_kernel_profile& t = P.tot[q.prec];
+        t.launches += 1;
+        t.ms += ms;
+        t.sites += q.sites;
+        t.hops += q.hops;
+        t.flops += q.flops;
+        t.bytes += q.bytes;
     }
     P.pending.clear();
     return GS_OK;
@@ -69,12 +70,23 @@ gs_status prof_begin(gs_ctx* c, int* slot) {
 }
 
 gs_status prof_end(gs_ctx* c, int slot, const Plan* p, const StencilArgs& a) {
+    long long hops;
+    double flops, bytes;
+    stencil_work(c, p, a, &hops, &flops, &bytes);
+    return prof_end_work(c, slot, GS_F64, a.n_out, hops, flops, bytes);
+}
+
+gs_status prof_end_work(gs_ctx* c, int slot, int prec, long long sites, long long hops,
+                        double flops, double bytes) {
     Profiler& P = c->prof;
     GS_CUDA(c, cudaEventRecord(P.ev[2 * slot + 1], c->stream));
     Profiler::Pending q;
     q.slot = slot;
-    q.sites = a.n_out;
-    stencil_work(c, p, a, &q.hops, &q.flops, &q.bytes);
+    q.prec = prec;
+    q.sites = sites;
+    q.hops = hops;
+    q.flops = flops;
+    q.bytes = bytes;
     P.pending.push_back(q);
     return GS_OK;
 }
@@ -97,7 +109,7 @@ gs_status gs_profile(gs_ctx* c, int enable) {
         }
         gs_status s = prof_harvest(c);
         if (s != GS_OK) return s;
-        P.tot = gs_kernel_profile{};
+        for (auto& t : P.tot) t = gs_kernel_profile{};
         P.on = true;
     } else {
         gs_status s = prof_harvest(c);
@@ -107,12 +119,14 @@ gs_status gs_profile(gs_ctx* c, int enable) {
     return GS_OK;
 }
 
-gs_status gs_profile_read(gs_ctx* c, gs_kernel_profile* out) {
+gs_status gs_profile_read(gs_ctx* c, int prec, gs_kernel_profile* out) {
     if (!c || !out) return GS_EINVAL;
+    if (prec != GS_F64 && prec != GS_F32 && prec != GS_BF16)
+        return set_err(c, GS_EINVAL, "unknown stencil precision %d", prec);
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     gs_status s = prof_harvest(c);
     if (s != GS_OK) return s;
-    *out = c->prof.tot;
+    *out = c->prof.tot[prec];
     return GS_OK;
 }
 

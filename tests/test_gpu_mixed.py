@@ -120,3 +120,57 @@ def test_lowp_tol_validation(env):
     with pytest.raises(gs.GschurError):
         ctx.schur_solve(1, 0, 0, z, z.clone(), gs.gs_default_opts(inner_prec=7))
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 4e-6), ("bf16", 3e-2)])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (3, 4, 2, 5)])
+def test_lowp_stencil_full_lattice(env, prec, tol, dims):
+    """wilson_apply_lowp (type 0, whole lattice) against the oracle's D in
+    FP64, to the rounding of the storage format (FP32: 2^-24, BF16: 2^-9 per
+    input, about 100 terms per output)."""
+    torch, gs = env
+    U = li.random_gauge(dims, 0.4, 3)
+    ctx = _ctx(gs, torch, dims, -0.2, U)
+    V = li.volume(dims)
+    p = gs.GS_F32 if prec == "f32" else gs.GS_BF16
+    x = li.gaussian_source(dims, 5)
+    xd = to_dev(x, torch)
+    xl = torch.empty(gs.lowp_bytes(V, p), dtype=torch.uint8, device="cuda:0")
+    yl = torch.empty_like(xl)
+    yd = torch.empty_like(xd)
+    ctx.lowp_pack(0, 0, 0, p, xd, xl)
+    ctx.wilson_apply_lowp(0, 0, 0, p, xl, yl)
+    ctx.lowp_unpack(0, 0, 0, p, yl, yd)
+    ref = (dirac.wilson_matrix(U, dims, -0.2) @ x.ravel()).reshape(x.shape)
+    got = yd.cpu().numpy()
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    # pack / unpack round trip is exact up to the storage rounding
+    back = torch.empty_like(xd)
+    ctx.lowp_unpack(0, 0, 0, p, xl, back)
+    assert np.abs(back.cpu().numpy() - x).max() <= (2 ** -8 if prec == "bf16" else 2 ** -23) * np.abs(x).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 4e-6), ("bf16", 3e-2)])
+@pytest.mark.parametrize("t,mu,inv", TYPES + [(2, 2, True)])
+def test_lowp_stencil_rest_set(env, prec, tol, t, mu, inv):
+    """wilson_apply_lowp on the rest set r: D_rr of P D P^T (Section 1)."""
+    torch, gs = env
+    dims = (4, 4, 4, 4)
+    U = li.random_gauge(dims, 0.3, 6)
+    ctx = _ctx(gs, torch, dims, 0.1, U)
+    perm, nb = permute.permutation(dims, t, mu, inv)
+    _, _, _, Drr = schur.partition(dirac.wilson_matrix(U, dims, 0.1), perm, nb)
+    n = li.volume(dims) - nb
+    p = gs.GS_F32 if prec == "f32" else gs.GS_BF16
+    z = li.gaussian_source(dims, 8).reshape(-1, 12)[:n].ravel()
+    zd = to_dev(z, torch)
+    zl = torch.empty(gs.lowp_bytes(n, p), dtype=torch.uint8, device="cuda:0")
+    yl = torch.empty_like(zl)
+    yd = torch.empty_like(zd)
+    ctx.lowp_pack(t, mu, int(inv), p, zd, zl)
+    ctx.wilson_apply_lowp(t, mu, int(inv), p, zl, yl)
+    ctx.lowp_unpack(t, mu, int(inv), p, yl, yd)
+    ref = Drr @ z
+    assert np.abs(yd.cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
+    ctx.close()
