@@ -360,17 +360,31 @@ __device__ __forceinline__ float2 cmulf2(float2 a, float2 b) {
 }
 
 // ---------------------------------------------------------------------------
-// the low-precision D_rr stencil (thread per site, all 8 hops in registers)
+// the low-precision stencil: a block of 4 warps covers 32 sites, warp w owns
+// direction mu = w (forward and backward hop) for all 32 sites.  All loads of
+// a warp's two hops are issued before any is used (out-of-set neighbours read
+// a valid dummy site and are masked afterwards), so each thread waits for
+// memory about twice instead of once per hop; the four 24-float partial
+// results meet in shared memory and are summed per 16-byte output group.
 // ---------------------------------------------------------------------------
+constexpr int kLpSites = 32;
+constexpr int kLpThreads = 128;
+
 template <class S, int MU>
-__device__ __forceinline__ void lp_hops(const LpArgs& a, int64_t k, float (&acc)[24]) {
-    const int2 nb = __ldg(a.nbr + k * 4 + MU);
-    if (nb.x >= 0) {
-        float p[24], lf[12];
+__device__ __forceinline__ void lp_dir(const LpArgs& a, int64_t k, bool valid, float (&acc)[24]) {
+#pragma unroll
+    for (int q = 0; q < 24; ++q) acc[q] = 0.f;
+    const int2 nb = valid ? __ldg(a.nbr + k * 4 + MU) : make_int2(-1, -1);
+    const bool hf = nb.x >= 0, hb = nb.y >= 0;
+    const int64_t jf = hf ? nb.x : 0, jb = hb ? nb.y : 0, jk = valid ? k : 0;
+    float pf[24], pb[24], lf[12], lb[12];
+    Store<S>::load_spinor(a.in, a.n, jf, pf);
+    Store<S>::load_spinor(a.in, a.n, jb, pb);
+    Store<S>::load_link(a.links, a.n, MU, jk, lf);
+    Store<S>::load_link(a.links, a.n, MU, jb, lb);
+    if (hf) {
         cf h[2][3], u[3][3], g[2][3];
-        Store<S>::load_spinor(a.in, a.n, nb.x, p);
-        Store<S>::load_link(a.links, a.n, MU, k, lf);
-        project<MU, true>(p, h);
+        project<MU, true>(pf, h);
         rebuild(lf, u);
 #pragma unroll
         for (int s = 0; s < 2; ++s)
@@ -383,13 +397,10 @@ __device__ __forceinline__ void lp_hops(const LpArgs& a, int64_t k, float (&acc)
             }
         accumulate<MU, -1>(acc, g);
     }
-    if (nb.y >= 0) {
-        float p[24], lf[12];
+    if (hb) {
         cf h[2][3], u[3][3], g[2][3];
-        Store<S>::load_spinor(a.in, a.n, nb.y, p);
-        Store<S>::load_link(a.links, a.n, MU, nb.y, lf);
-        project<MU, false>(p, h);
-        rebuild(lf, u);
+        project<MU, false>(pb, h);
+        rebuild(lb, u);
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -404,45 +415,99 @@ __device__ __forceinline__ void lp_hops(const LpArgs& a, int64_t k, float (&acc)
     }
 }
 
+// One 16-byte output group (4 reals for FP32, 8 for BF16) of site k.
+template <class S>
+struct Group;
+template <>
+struct Group<float> {
+    static constexpr int kReals = 4, kGroups = 6;
+    __device__ __forceinline__ static void load(const void* b, int64_t n, int g, int64_t k,
+                                                float (&f)[8]) {
+        const float4 v = __ldg((const float4*)b + g * n + k);
+        f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
+    }
+    __device__ __forceinline__ static void store(void* b, int64_t n, int g, int64_t k,
+                                                 const float (&f)[8]) {
+        ((float4*)b)[g * n + k] = make_float4(f[0], f[1], f[2], f[3]);
+    }
+};
+template <>
+struct Group<__nv_bfloat16> {
+    static constexpr int kReals = 8, kGroups = 3;
+    __device__ __forceinline__ static void load(const void* b, int64_t n, int g, int64_t k,
+                                                float (&f)[8]) {
+        const uint4 v = __ldg((const uint4*)b + g * n + k);
+        float2 t;
+        t = unpack_bf2(v.x); f[0] = t.x; f[1] = t.y;
+        t = unpack_bf2(v.y); f[2] = t.x; f[3] = t.y;
+        t = unpack_bf2(v.z); f[4] = t.x; f[5] = t.y;
+        t = unpack_bf2(v.w); f[6] = t.x; f[7] = t.y;
+    }
+    __device__ __forceinline__ static void store(void* b, int64_t n, int g, int64_t k,
+                                                 const float (&f)[8]) {
+        ((uint4*)b)[g * n + k] = make_uint4(pack_bf2(f[0], f[1]), pack_bf2(f[2], f[3]),
+                                            pack_bf2(f[4], f[5]), pack_bf2(f[6], f[7]));
+    }
+};
+
 template <class S, int EPI>
-__global__ void k_dslash_lp(LpArgs a) {
+__global__ void __launch_bounds__(kLpThreads) k_dslash_lp(LpArgs a) {
     const bool skip = a.st != nullptr && a.st->done;
     if (a.ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *a.ran = skip ? 0 : 1;
     if (skip) return;
+    __shared__ float red[4][24][kLpSites];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float e[3] = {0.f, 0.f, 0.f};
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        float acc[24];
-#pragma unroll
-        for (int q = 0; q < 24; ++q) acc[q] = 0.f;
-        lp_hops<S, 0>(a, k, acc);
-        lp_hops<S, 1>(a, k, acc);
-        lp_hops<S, 2>(a, k, acc);
-        lp_hops<S, 3>(a, k, acc);
-        float self[24];
-        Store<S>::load_spinor(a.in, a.n, k, self);
-#pragma unroll
-        for (int q = 0; q < 24; ++q) acc[q] = fmaf(a.diag, self[q], acc[q]);
-        Store<S>::store_spinor(a.out, a.n, k, acc);
-        if (EPI == EPI_DOT_RHAT_V) {  // <rhat, v>
-            float rv[24];
-            Store<S>::load_spinor(a.epi_vec, a.n, k, rv);
-#pragma unroll
-            for (int q = 0; q < 12; ++q) {
-                e[0] = fmaf(rv[2 * q], acc[2 * q], fmaf(rv[2 * q + 1], acc[2 * q + 1], e[0]));
-                e[1] = fmaf(rv[2 * q], acc[2 * q + 1], fmaf(-rv[2 * q + 1], acc[2 * q], e[1]));
+    constexpr int R = Group<S>::kReals, G = Group<S>::kGroups;
+    for (int64_t base = (int64_t)blockIdx.x * kLpSites; base < a.n;
+         base += (int64_t)gridDim.x * kLpSites) {
+        const int64_t k = base + lane;
+        const bool valid = k < a.n;
+        {
+            float acc[24];
+            switch (warp) {
+                case 0: lp_dir<S, 0>(a, k, valid, acc); break;
+                case 1: lp_dir<S, 1>(a, k, valid, acc); break;
+                case 2: lp_dir<S, 2>(a, k, valid, acc); break;
+                default: lp_dir<S, 3>(a, k, valid, acc); break;
             }
-        } else if (EPI == EPI_DOT_TS) {  // <t, s>, <t, t>
-            float sv[24];
-            Store<S>::load_spinor(a.epi_vec, a.n, k, sv);
 #pragma unroll
-            for (int q = 0; q < 12; ++q) {
-                const float tr = acc[2 * q], ti = acc[2 * q + 1];
-                e[0] = fmaf(tr, sv[2 * q], fmaf(ti, sv[2 * q + 1], e[0]));
-                e[1] = fmaf(tr, sv[2 * q + 1], fmaf(-ti, sv[2 * q], e[1]));
-                e[2] = fmaf(tr, tr, fmaf(ti, ti, e[2]));
+            for (int q = 0; q < 24; ++q) red[warp][q][lane] = acc[q];
+        }
+        __syncthreads();
+        if (valid) {
+            for (int g = warp; g < G; g += 4) {
+                float self[8], out[8];
+                Group<S>::load(a.in, a.n, g, k, self);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const int q = g * R + j;
+                    out[j] = fmaf(a.diag, self[j],
+                                  (red[0][q][lane] + red[1][q][lane]) + (red[2][q][lane] + red[3][q][lane]));
+                }
+                Group<S>::store(a.out, a.n, g, k, out);
+                if (EPI == EPI_DOT_RHAT_V) {  // <rhat, v>
+                    float rv[8];
+                    Group<S>::load(a.epi_vec, a.n, g, k, rv);
+#pragma unroll
+                    for (int j = 0; j < R; j += 2) {
+                        e[0] = fmaf(rv[j], out[j], fmaf(rv[j + 1], out[j + 1], e[0]));
+                        e[1] = fmaf(rv[j], out[j + 1], fmaf(-rv[j + 1], out[j], e[1]));
+                    }
+                } else if (EPI == EPI_DOT_TS) {  // <t, s>, <t, t>
+                    float sv[8];
+                    Group<S>::load(a.epi_vec, a.n, g, k, sv);
+#pragma unroll
+                    for (int j = 0; j < R; j += 2) {
+                        const float tr = out[j], ti = out[j + 1];
+                        e[0] = fmaf(tr, sv[j], fmaf(ti, sv[j + 1], e[0]));
+                        e[1] = fmaf(tr, sv[j + 1], fmaf(-ti, sv[j], e[1]));
+                        e[2] = fmaf(tr, tr, fmaf(ti, ti, e[2]));
+                    }
+                }
             }
         }
+        __syncthreads();
     }
     if constexpr (EPI == EPI_NONE) {
         return;
@@ -725,8 +790,8 @@ gs_status launch_lp_stencil(gs_ctx* c, LpArgs a, long long hops, long long* laun
         if (s != GS_OK) return s;
         a.ran = c->prof.ran_dev + slot;
     }
-    const int b = lp_block(a.n, c->num_sms);
-    int64_t g = (a.n + b - 1) / b;
+    const int b = kLpThreads;
+    int64_t g = (a.n + kLpSites - 1) / kLpSites;
     if (a.epi != EPI_NONE && g > kMaxRedBlocks) g = kMaxRedBlocks;
     switch (a.epi) {
         case EPI_NONE: k_dslash_lp<S, EPI_NONE><<<(int)g, b, 0, c->stream>>>(a); break;
