@@ -228,6 +228,7 @@ def kernel_case(args):
         run = lambda: ctx.wilson_apply(x, y)   # noqa: E731
     else:
         prec = gs.GS_F32 if args.prec == "f32" else gs.GS_BF16
+        ctx.set_option(gs.GS_OPT_STENCIL_VARIANT, args.variant)
         xl = torch.empty(gs.lowp_bytes(V, prec), dtype=torch.uint8, device=dev)
         yl = torch.empty_like(xl)
         ctx.lowp_pack(0, 0, 0, prec, x, xl)
@@ -243,6 +244,7 @@ def kernel_case(args):
     ms = p.ms / p.launches
     peaks = _peaks()
     out = {"case": args.case, "prec": args.prec if args.case != "wilson_f64" else "f64",
+           "variant": ctx.get_option(gs.GS_OPT_STENCIL_VARIANT) if args.case != "wilson_f64" else None,
            "dims": dims, "sites": V, "launches": p.launches,
            "us_per_launch": 1e3 * ms, "sites_per_s": V / (ms / 1e3),
            "tflops": p.flops / p.launches / (ms / 1e3) / 1e12,
@@ -266,6 +268,8 @@ def main():
     ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp"],
                     help="kernel micro-benchmark instead of the solve (for profiling)")
     ap.add_argument("--prec", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
+                    help="low-precision stencil variant (0 = autotuned)")
     ap.add_argument("--dims", default="24,24,24,48")
     ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()

@@ -21,12 +21,14 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOMEM", 3: "GS_MAXITER",
 GS_TYPE_I, GS_TYPE_II = 1, 2
 GS_F64, GS_F32, GS_BF16 = 0, 1, 2
 GS_GMRES, GS_BICGSTAB = 0, 1
+GS_OPT_STENCIL_VARIANT = 1
 
 # every symbol the header declares
 EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson_apply",
            "permute_sites", "gs_get_permutation", "schur_apply", "schur_solve",
            "gs_last_error", "gs_version", "gs_profile", "gs_profile_read",
-           "wilson_apply_noalloc", "gs_lowp_pack", "gs_lowp_unpack", "wilson_apply_lowp")
+           "wilson_apply_noalloc", "gs_lowp_pack", "gs_lowp_unpack", "wilson_apply_lowp", "gs_set_option",
+           "gs_get_option")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -84,6 +86,8 @@ def _load():
                                        vp, vp]),
         "gs_profile_read": (i32, [vp, i32, ctypes.POINTER(gs_kernel_profile)]),
         "gs_lowp_pack": (i32, [vp, i32, i32, i32, i32, vp, vp]),
+        "gs_set_option": (i32, [vp, i32, i32]),
+        "gs_get_option": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int)]),
         "gs_lowp_unpack": (i32, [vp, i32, i32, i32, i32, vp, vp]),
         "wilson_apply_lowp": (i32, [vp, i32, i32, i32, i32, vp, vp]),
     }
@@ -208,6 +212,16 @@ def gs_profile_read(ctx, prec=GS_F64):
     return out
 
 
+def gs_set_option(ctx, option, value):
+    return _check(ctx, lib.gs_set_option(ctx, option, value))
+
+
+def gs_get_option(ctx, option):
+    v = ctypes.c_int()
+    _check(ctx, lib.gs_get_option(ctx, option, ctypes.byref(v)))
+    return v.value
+
+
 def lowp_bytes(n_sites, prec):
     """Size of a low-precision vector of n sites."""
     return n_sites * (48 if prec == GS_BF16 else 96)
@@ -276,6 +290,12 @@ class Context:
 
     def profile_read(self, prec=GS_F64):
         return gs_profile_read(self.handle, prec)
+
+    def set_option(self, option, value):
+        return gs_set_option(self.handle, option, value)
+
+    def get_option(self, option):
+        return gs_get_option(self.handle, option)
 
     def lowp_pack(self, ptype, dir, inverse, prec, x, x_lp):
         return gs_lowp_pack(self.handle, ptype, dir, inverse, prec, x, x_lp)

@@ -154,6 +154,26 @@ gs_status gs_destroy(gs_ctx* c) {
     return GS_OK;
 }
 
+gs_status gs_set_option(gs_ctx* c, int option, int value) {
+    if (!c) return GS_EINVAL;
+    if (option == GS_OPT_STENCIL_VARIANT) {
+        if (value < 0 || value > 2) return set_err(c, GS_EINVAL, "stencil variant %d not in 0..2", value);
+        c->opt_stencil_variant = value;
+        invalidate_mixed_links(c);  // re-tune / re-select on next use
+        return GS_OK;
+    }
+    return set_err(c, GS_EINVAL, "unknown option %d", option);
+}
+
+gs_status gs_get_option(gs_ctx* c, int option, int* value) {
+    if (!c || !value) return GS_EINVAL;
+    if (option == GS_OPT_STENCIL_VARIANT) {
+        *value = c->opt_stencil_variant ? c->opt_stencil_variant : c->tuned_variant;
+        return GS_OK;
+    }
+    return set_err(c, GS_EINVAL, "unknown option %d", option);
+}
+
 gs_status gs_set_gauge(gs_ctx* c, const void* U_dev) {
     if (check_ctx(c) != GS_OK) return GS_EINVAL;
     if (!U_dev) return set_err(c, GS_EINVAL, "null gauge field");

@@ -194,6 +194,8 @@ struct gs_ctx {
     long long stencil_sites = 0;
     gs::Profiler prof;
     void* mixed = nullptr;             // mixed-precision state (mixed.cu)
+    int opt_stencil_variant = 0;       // 0 = autotune, 1 = site, 2 = direction
+    int tuned_variant = 0;             // the variant the autotuner picked last
     std::string err;
 };
 

@@ -415,6 +415,105 @@ __device__ __forceinline__ void lp_dir(const LpArgs& a, int64_t k, bool valid, f
     }
 }
 
+// Variant "site": one thread per site, all eight hops in registers.  The
+// neighbour indices of all four directions are loaded first; each direction's
+// two spinors and two links are then loaded together (out-of-set neighbours
+// read a valid dummy site and are masked), so a thread waits for memory about
+// five times per site instead of sixteen.
+template <class S, int MU>
+__device__ __forceinline__ void site_dir(const LpArgs& a, int64_t k, int2 nb, float (&acc)[24]) {
+    const bool hf = nb.x >= 0, hb = nb.y >= 0;
+    const int64_t jf = hf ? nb.x : k, jb = hb ? nb.y : k;
+    float pf[24], pb[24], lf[12], lb[12];
+    Store<S>::load_spinor(a.in, a.n, jf, pf);
+    Store<S>::load_spinor(a.in, a.n, jb, pb);
+    Store<S>::load_link(a.links, a.n, MU, k, lf);
+    Store<S>::load_link(a.links, a.n, MU, jb, lb);
+    if (hf) {
+        cf h[2][3], u[3][3], g[2][3];
+        project<MU, true>(pf, h);
+        rebuild(lf, u);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                cf t = cmul(u[r][0], h[s][0]);
+                cfma_(t, u[r][1], h[s][1]);
+                cfma_(t, u[r][2], h[s][2]);
+                g[s][r] = t;
+            }
+        accumulate<MU, -1>(acc, g);
+    }
+    if (hb) {
+        cf h[2][3], u[3][3], g[2][3];
+        project<MU, false>(pb, h);
+        rebuild(lb, u);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                cf t = cf{0.f, 0.f};
+                ccfma_(t, u[0][r], h[s][0]);
+                ccfma_(t, u[1][r], h[s][1]);
+                ccfma_(t, u[2][r], h[s][2]);
+                g[s][r] = t;
+            }
+        accumulate<MU, +1>(acc, g);
+    }
+}
+
+template <class S, int EPI>
+__device__ __forceinline__ void lp_finish(const LpArgs& a, LpState* st, float (&tot)[3]);
+
+template <class S, int EPI>
+__global__ void __launch_bounds__(128) k_dslash_lp_site(LpArgs a) {
+    const bool skip = a.st != nullptr && a.st->done;
+    if (a.ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *a.ran = skip ? 0 : 1;
+    if (skip) return;
+    float e[3] = {0.f, 0.f, 0.f};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int4 n01 = __ldg((const int4*)(a.nbr + k * 4));
+        const int4 n23 = __ldg((const int4*)(a.nbr + k * 4) + 1);
+        float acc[24];
+#pragma unroll
+        for (int q = 0; q < 24; ++q) acc[q] = 0.f;
+        site_dir<S, 0>(a, k, make_int2(n01.x, n01.y), acc);
+        site_dir<S, 1>(a, k, make_int2(n01.z, n01.w), acc);
+        site_dir<S, 2>(a, k, make_int2(n23.x, n23.y), acc);
+        site_dir<S, 3>(a, k, make_int2(n23.z, n23.w), acc);
+        float self[24];
+        Store<S>::load_spinor(a.in, a.n, k, self);
+#pragma unroll
+        for (int q = 0; q < 24; ++q) acc[q] = fmaf(a.diag, self[q], acc[q]);
+        Store<S>::store_spinor(a.out, a.n, k, acc);
+        if (EPI == EPI_DOT_RHAT_V) {
+            float rv[24];
+            Store<S>::load_spinor(a.epi_vec, a.n, k, rv);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                e[0] = fmaf(rv[2 * q], acc[2 * q], fmaf(rv[2 * q + 1], acc[2 * q + 1], e[0]));
+                e[1] = fmaf(rv[2 * q], acc[2 * q + 1], fmaf(-rv[2 * q + 1], acc[2 * q], e[1]));
+            }
+        } else if (EPI == EPI_DOT_TS) {
+            float sv[24];
+            Store<S>::load_spinor(a.epi_vec, a.n, k, sv);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                const float tr = acc[2 * q], ti = acc[2 * q + 1];
+                e[0] = fmaf(tr, sv[2 * q], fmaf(ti, sv[2 * q + 1], e[0]));
+                e[1] = fmaf(tr, sv[2 * q + 1], fmaf(-ti, sv[2 * q], e[1]));
+                e[2] = fmaf(tr, tr, fmaf(ti, ti, e[2]));
+            }
+        }
+    }
+    if constexpr (EPI != EPI_NONE) {
+        float tot[3];
+        if (lp_reduce_last<3>(e, a.partial, a.counter, tot) && threadIdx.x == 0)
+            lp_finish<S, EPI>(a, a.st, tot);
+    }
+}
+
 // One 16-byte output group (4 reals for FP32, 8 for BF16) of site k.
 template <class S>
 struct Group;
@@ -451,7 +550,7 @@ struct Group<__nv_bfloat16> {
 };
 
 template <class S, int EPI>
-__global__ void __launch_bounds__(kLpThreads) k_dslash_lp(LpArgs a) {
+__global__ void __launch_bounds__(kLpThreads) k_dslash_lp_dir(LpArgs a) {
     const bool skip = a.st != nullptr && a.st->done;
     if (a.ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *a.ran = skip ? 0 : 1;
     if (skip) return;
@@ -513,31 +612,35 @@ __global__ void __launch_bounds__(kLpThreads) k_dslash_lp(LpArgs a) {
         return;
     } else {
         float tot[3];
-        if (lp_reduce_last<3>(e, a.partial, a.counter, tot) && threadIdx.x == 0) {
-            LpState* st = a.st;
-            if (EPI == EPI_DOT_RHAT_V) {
-                const float2 den = make_float2(tot[0], tot[1]);
-                if (den.x == 0.f && den.y == 0.f) {
-                    st->status = GS_BREAKDOWN;
-                    st->done = 1;
-                } else {
-                    st->alpha = cdivf_(st->rho, den);
-                    if (!isfinite(st->alpha.x) || !isfinite(st->alpha.y)) {
-                        st->status = GS_NONFINITE;
-                        st->done = 1;
-                    }
-                }
-            } else {
-                st->omega = tot[2] > 0.f ? make_float2(tot[0] / tot[2], tot[1] / tot[2])
-                                         : make_float2(0.f, 0.f);
-                if (!isfinite(st->omega.x) || !isfinite(st->omega.y)) {
-                    st->status = GS_NONFINITE;
-                    st->done = 1;
-                }
+        if (lp_reduce_last<3>(e, a.partial, a.counter, tot) && threadIdx.x == 0)
+            lp_finish<S, EPI>(a, a.st, tot);
+    }
+}
+
+// alpha = rho / <rhat, v>  or  omega = <t, s> / <t, t>, in the last block
+template <class S, int EPI>
+__device__ __forceinline__ void lp_finish(const LpArgs& a, LpState* st, float (&tot)[3]) {
+    if (EPI == EPI_DOT_RHAT_V) {
+        const float2 den = make_float2(tot[0], tot[1]);
+        if (den.x == 0.f && den.y == 0.f) {
+            st->status = GS_BREAKDOWN;
+            st->done = 1;
+        } else {
+            st->alpha = cdivf_(st->rho, den);
+            if (!isfinite(st->alpha.x) || !isfinite(st->alpha.y)) {
+                st->status = GS_NONFINITE;
+                st->done = 1;
             }
-            if (st->done) lp_publish(st);
+        }
+    } else {
+        st->omega = tot[2] > 0.f ? make_float2(tot[0] / tot[2], tot[1] / tot[2])
+                                 : make_float2(0.f, 0.f);
+        if (!isfinite(st->omega.x) || !isfinite(st->omega.y)) {
+            st->status = GS_NONFINITE;
+            st->done = 1;
         }
     }
+    if (st->done) lp_publish(st);
 }
 
 // ---------------------------------------------------------------------------
@@ -778,11 +881,12 @@ int lp_block(int64_t n, int sms) {
     return 32;
 }
 
-// Launch the low-precision stencil; with profiling on, bracket it by events
-// and count its algorithmic work (168 flop per in-set hop + 48 per site;
-// bytes: spinor in + out, one link read per link used, each datum once).
+// Launch the low-precision stencil (variant 1: thread per site; 2: warp per
+// direction); with profiling on, bracket it by events and count its
+// algorithmic work (168 flop per in-set hop + 48 per site; bytes: spinor in +
+// out, one 12-real link per link used, each datum once).
 template <class S>
-gs_status launch_lp_stencil(gs_ctx* c, LpArgs a, long long hops, long long* launches) {
+gs_status launch_lp_stencil(gs_ctx* c, LpArgs a, long long hops, int variant, long long* launches) {
     int slot = -1;
     a.ran = nullptr;
     if (c->prof.on) {
@@ -790,13 +894,23 @@ gs_status launch_lp_stencil(gs_ctx* c, LpArgs a, long long hops, long long* laun
         if (s != GS_OK) return s;
         a.ran = c->prof.ran_dev + slot;
     }
-    const int b = kLpThreads;
-    int64_t g = (a.n + kLpSites - 1) / kLpSites;
-    if (a.epi != EPI_NONE && g > kMaxRedBlocks) g = kMaxRedBlocks;
-    switch (a.epi) {
-        case EPI_NONE: k_dslash_lp<S, EPI_NONE><<<(int)g, b, 0, c->stream>>>(a); break;
-        case EPI_DOT_RHAT_V: k_dslash_lp<S, EPI_DOT_RHAT_V><<<(int)g, b, 0, c->stream>>>(a); break;
-        default: k_dslash_lp<S, EPI_DOT_TS><<<(int)g, b, 0, c->stream>>>(a); break;
+    if (variant == 2) {
+        int64_t g = (a.n + kLpSites - 1) / kLpSites;
+        if (a.epi != EPI_NONE && g > kMaxRedBlocks) g = kMaxRedBlocks;
+        switch (a.epi) {
+            case EPI_NONE: k_dslash_lp_dir<S, EPI_NONE><<<(int)g, kLpThreads, 0, c->stream>>>(a); break;
+            case EPI_DOT_RHAT_V: k_dslash_lp_dir<S, EPI_DOT_RHAT_V><<<(int)g, kLpThreads, 0, c->stream>>>(a); break;
+            default: k_dslash_lp_dir<S, EPI_DOT_TS><<<(int)g, kLpThreads, 0, c->stream>>>(a); break;
+        }
+    } else {
+        const int b = lp_block(a.n, c->num_sms);
+        int64_t g = (a.n + b - 1) / b;
+        if (a.epi != EPI_NONE && g > kMaxRedBlocks) g = kMaxRedBlocks;
+        switch (a.epi) {
+            case EPI_NONE: k_dslash_lp_site<S, EPI_NONE><<<(int)g, b, 0, c->stream>>>(a); break;
+            case EPI_DOT_RHAT_V: k_dslash_lp_site<S, EPI_DOT_RHAT_V><<<(int)g, b, 0, c->stream>>>(a); break;
+            default: k_dslash_lp_site<S, EPI_DOT_TS><<<(int)g, b, 0, c->stream>>>(a); break;
+        }
     }
     ++*launches;
     GS_CHECK_LAUNCH(c);
@@ -833,11 +947,13 @@ struct LpPlanData {
     int64_t nb = 0;        // labels below nb are excluded (0 for the full lattice)
     int64_t n = 0;         // sites of the set
     long long hops = 0;    // in-set neighbour terms of one D application
+    int variant = 0;       // stencil variant: 1 = thread per site, 2 = warp per direction
     int2* nbr_r = nullptr;
     void* links = nullptr;
 };
 
 static size_t spinor_bytes(int prec) { return prec == GS_BF16 ? 48 : 96; }
+static gs_status ensure_lp(gs_ctx* c, int prec, int64_t n);
 static size_t link_bytes(int prec) { return prec == GS_BF16 ? 24 : 48; }
 
 struct MixedState {
@@ -910,6 +1026,60 @@ static gs_status ensure_lp(gs_ctx* c, int prec, int64_t n) {
     return GS_OK;
 }
 
+// The autotuner: time both stencil variants on this set (2 warm-up and 5
+// timed launches each, CUDA events, zeroed operands) and keep the faster one;
+// a variant forced with gs_set_option skips the timing.
+static gs_status lp_tune(gs_ctx* c, LpPlanData& pd) {
+    if (c->opt_stencil_variant == 1 || c->opt_stencil_variant == 2) {
+        pd.variant = c->opt_stencil_variant;
+        return GS_OK;
+    }
+    gs_status s = ensure_lp(c, pd.prec, pd.n);
+    if (s != GS_OK) return s;
+    MixedState* m = mixed_of(c);
+    const size_t bytes = (size_t)pd.n * spinor_bytes(pd.prec);
+    GS_CUDA(c, cudaMemsetAsync(m->w.p, 0, bytes, c->stream));
+    LpArgs a;
+    memset(&a, 0, sizeof a);
+    a.out = m->w.v;
+    a.in = m->w.p;
+    a.links = pd.links;
+    a.nbr = pd.nbr_r;
+    a.n = pd.n;
+    a.diag = (float)(c->m0 + 4.0);
+    a.epi = EPI_NONE;
+    cudaEvent_t e0, e1;
+    GS_CUDA(c, cudaEventCreate(&e0));
+    GS_CUDA(c, cudaEventCreate(&e1));
+    float best = 0.f;
+    const bool was_on = c->prof.on;
+    c->prof.on = false;
+    for (int v = 1; v <= 2; ++v) {
+        long long l = 0;
+        for (int r = 0; r < 7; ++r) {
+            if (r == 2) GS_CUDA(c, cudaEventRecord(e0, c->stream));
+            s = (pd.prec == GS_BF16) ? launch_lp_stencil<__nv_bfloat16>(c, a, pd.hops, v, &l)
+                                     : launch_lp_stencil<float>(c, a, pd.hops, v, &l);
+            if (s != GS_OK) break;
+        }
+        c->launches += l;
+        if (s != GS_OK) break;
+        GS_CUDA(c, cudaEventRecord(e1, c->stream));
+        GS_CUDA(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        GS_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (v == 1 || ms < best) {
+            best = ms;
+            pd.variant = v;
+        }
+    }
+    c->prof.on = was_on;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tuned_variant = pd.variant;
+    return s;
+}
+
 static gs_status lp_plan(gs_ctx* c, const Plan* p, int prec, LpPlanData** out) {
     MixedState* m = mixed_of(c);
     for (auto& pd : m->plans)
@@ -938,6 +1108,8 @@ static gs_status lp_plan(gs_ctx* c, const Plan* p, int prec, LpPlanData** out) {
         k_lp_tables<float><<<g, 256, 0, c->stream>>>(pd.nb, n, p->nbr, p->links, pd.nbr_r, pd.links);
     c->launches++;
     GS_CHECK_LAUNCH(c);
+    gs_status s = lp_tune(c, pd);
+    if (s != GS_OK) return s;
     m->plans.push_back(pd);
     *out = &m->plans.back();
     return GS_OK;
@@ -992,10 +1164,10 @@ static gs_status lp_bicgstab(gs_ctx* c, LpPlanData* pd, int64_t n, float tol, in
                 GS_CUDA(c, cudaEventSynchronize(iw.ev[(it - depth) % 4]));
                 if (pub->done) break;
             }
-            if ((s = launch_lp_stencil<S>(c, k1, pd->hops, &dummy)) != GS_OK) return s;
+            if ((s = launch_lp_stencil<S>(c, k1, pd->hops, pd->variant, &dummy)) != GS_OK) return s;
             k_lp_s<S><<<gr, bb, 0, c->stream>>>(w.r, w.v, w.p, w.s, w.x, n, w.st, w.partial,
                                                  w.counter);
-            if ((s = launch_lp_stencil<S>(c, k3, pd->hops, &dummy)) != GS_OK) return s;
+            if ((s = launch_lp_stencil<S>(c, k3, pd->hops, pd->variant, &dummy)) != GS_OK) return s;
             k_lp_xr<S><<<gr, bb, 0, c->stream>>>(w.s, w.t, w.rhat, w.x, w.r, n, w.st, w.partial,
                                                   w.counter);
             k_lp_p<S><<<gp, bb, 0, c->stream>>>(w.r, w.v, w.p, n, w.st);
@@ -1201,8 +1373,8 @@ gs_status wilson_apply_lowp(gs_ctx* c, int type, int dir, int inverse, int prec,
     a.diag = (float)(c->m0 + 4.0);
     a.epi = EPI_NONE;
     long long launches = 0;
-    s = (prec == GS_BF16) ? launch_lp_stencil<__nv_bfloat16>(c, a, pd->hops, &launches)
-                          : launch_lp_stencil<float>(c, a, pd->hops, &launches);
+    s = (prec == GS_BF16) ? launch_lp_stencil<__nv_bfloat16>(c, a, pd->hops, pd->variant, &launches)
+                          : launch_lp_stencil<float>(c, a, pd->hops, pd->variant, &launches);
     c->launches += launches;
     c->stencil_sites += pd->n;
     return s;

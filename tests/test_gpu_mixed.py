@@ -122,15 +122,17 @@ def test_lowp_tol_validation(env):
     ctx.close()
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("prec,tol", [("f32", 4e-6), ("bf16", 3e-2)])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (3, 4, 2, 5)])
-def test_lowp_stencil_full_lattice(env, prec, tol, dims):
+def test_lowp_stencil_full_lattice(env, prec, tol, dims, variant):
     """wilson_apply_lowp (type 0, whole lattice) against the oracle's D in
     FP64, to the rounding of the storage format (FP32: 2^-24, BF16: 2^-9 per
     input, about 100 terms per output)."""
     torch, gs = env
     U = li.random_gauge(dims, 0.4, 3)
     ctx = _ctx(gs, torch, dims, -0.2, U)
+    ctx.set_option(gs.GS_OPT_STENCIL_VARIANT, variant)
     V = li.volume(dims)
     p = gs.GS_F32 if prec == "f32" else gs.GS_BF16
     x = li.gaussian_source(dims, 5)
@@ -151,14 +153,16 @@ def test_lowp_stencil_full_lattice(env, prec, tol, dims):
     ctx.close()
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("prec,tol", [("f32", 4e-6), ("bf16", 3e-2)])
 @pytest.mark.parametrize("t,mu,inv", TYPES + [(2, 2, True)])
-def test_lowp_stencil_rest_set(env, prec, tol, t, mu, inv):
+def test_lowp_stencil_rest_set(env, prec, tol, t, mu, inv, variant):
     """wilson_apply_lowp on the rest set r: D_rr of P D P^T (Section 1)."""
     torch, gs = env
     dims = (4, 4, 4, 4)
     U = li.random_gauge(dims, 0.3, 6)
     ctx = _ctx(gs, torch, dims, 0.1, U)
+    ctx.set_option(gs.GS_OPT_STENCIL_VARIANT, variant)
     perm, nb = permute.permutation(dims, t, mu, inv)
     _, _, _, Drr = schur.partition(dirac.wilson_matrix(U, dims, 0.1), perm, nb)
     n = li.volume(dims) - nb
@@ -173,4 +177,20 @@ def test_lowp_stencil_rest_set(env, prec, tol, t, mu, inv):
     ctx.lowp_unpack(t, mu, int(inv), p, yl, yd)
     ref = Drr @ z
     assert np.abs(yd.cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
+    ctx.close()
+
+
+def test_autotuner_picks_a_variant_and_options_validate(env):
+    torch, gs = env
+    dims = (8, 8, 4, 4)
+    ctx = _ctx(gs, torch, dims, 0.1, li.random_gauge(dims, 0.3, 2))
+    V = li.volume(dims)
+    x = to_dev(li.gaussian_source(dims, 1), torch)
+    xl = torch.empty(gs.lowp_bytes(V, gs.GS_F32), dtype=torch.uint8, device="cuda:0")
+    ctx.lowp_pack(0, 0, 0, gs.GS_F32, x, xl)
+    assert ctx.get_option(gs.GS_OPT_STENCIL_VARIANT) in (1, 2)
+    with pytest.raises(gs.GschurError):
+        ctx.set_option(gs.GS_OPT_STENCIL_VARIANT, 5)
+    with pytest.raises(gs.GschurError):
+        ctx.set_option(99, 0)
     ctx.close()
