@@ -268,7 +268,7 @@ def main():
     ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp"],
                     help="kernel micro-benchmark instead of the solve (for profiling)")
     ap.add_argument("--prec", default="f32", choices=["f32", "bf16"])
-    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="low-precision stencil variant (0 = autotuned)")
     ap.add_argument("--dims", default="24,24,24,48")
     ap.add_argument("--reps", type=int, default=20)

@@ -121,11 +121,13 @@ gs_status gs_set_gauge(gs_ctx* ctx, const void* U_dev);
 
 /* Context options.
  * GS_OPT_STENCIL_VARIANT selects the low-precision stencil kernel: 0 = chosen
- * by the library's autotuner per set and precision (the default: both
- * variants are timed with CUDA events when a set is first used), 1 = one
- * thread per site (all eight hops in registers), 2 = one warp per direction
- * (four partial sums combined in shared memory).  gs_get_option returns the
- * forced value, or under autotuning the variant chosen most recently. */
+ * by the library's autotuner per set and precision (the default: every
+ * variant is timed with CUDA events when a set is first used), 1 = one
+ * thread per site (all eight hops in registers), 3 / 4 = the same with a
+ * register budget for 6 / 8 blocks of 128 threads per SM, 2 = one warp per
+ * direction (four partial sums combined in shared memory).  gs_get_option
+ * returns the forced value, or under autotuning the variant chosen most
+ * recently. */
 enum { GS_OPT_STENCIL_VARIANT = 1 };
 gs_status gs_set_option(gs_ctx* ctx, int option, int value);
 gs_status gs_get_option(gs_ctx* ctx, int option, int* value);

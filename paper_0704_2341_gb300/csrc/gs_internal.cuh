@@ -194,7 +194,7 @@ struct gs_ctx {
     long long stencil_sites = 0;
     gs::Profiler prof;
     void* mixed = nullptr;             // mixed-precision state (mixed.cu)
-    int opt_stencil_variant = 0;       // 0 = autotune, 1 = site, 2 = direction
+    int opt_stencil_variant = 0;       // 0 = autotune, 1/3/4 = site (4/6/8 blocks), 2 = direction
     int tuned_variant = 0;             // the variant the autotuner picked last
     std::string err;
 };

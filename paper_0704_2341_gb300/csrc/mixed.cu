@@ -465,8 +465,8 @@ __device__ __forceinline__ void site_dir(const LpArgs& a, int64_t k, int2 nb, fl
 template <class S, int EPI>
 __device__ __forceinline__ void lp_finish(const LpArgs& a, LpState* st, float (&tot)[3]);
 
-template <class S, int EPI>
-__global__ void __launch_bounds__(128) k_dslash_lp_site(LpArgs a) {
+template <class S, int EPI, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_dslash_lp_site(LpArgs a) {
     const bool skip = a.st != nullptr && a.st->done;
     if (a.ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *a.ran = skip ? 0 : 1;
     if (skip) return;
@@ -903,14 +903,26 @@ gs_status launch_lp_stencil(gs_ctx* c, LpArgs a, long long hops, int variant, lo
             default: k_dslash_lp_dir<S, EPI_DOT_TS><<<(int)g, kLpThreads, 0, c->stream>>>(a); break;
         }
     } else {
+        // variants 1, 3, 4: thread per site with a register budget for
+        // 4, 6 or 8 blocks of 128 threads per SM
         const int b = lp_block(a.n, c->num_sms);
         int64_t g = (a.n + b - 1) / b;
         if (a.epi != EPI_NONE && g > kMaxRedBlocks) g = kMaxRedBlocks;
-        switch (a.epi) {
-            case EPI_NONE: k_dslash_lp_site<S, EPI_NONE><<<(int)g, b, 0, c->stream>>>(a); break;
-            case EPI_DOT_RHAT_V: k_dslash_lp_site<S, EPI_DOT_RHAT_V><<<(int)g, b, 0, c->stream>>>(a); break;
-            default: k_dslash_lp_site<S, EPI_DOT_TS><<<(int)g, b, 0, c->stream>>>(a); break;
+#define GS_SITE_LAUNCH(MB)                                                                       \
+        switch (a.epi) {                                                                         \
+            case EPI_NONE: k_dslash_lp_site<S, EPI_NONE, MB><<<(int)g, b, 0, c->stream>>>(a); break; \
+            case EPI_DOT_RHAT_V:                                                                 \
+                k_dslash_lp_site<S, EPI_DOT_RHAT_V, MB><<<(int)g, b, 0, c->stream>>>(a); break;  \
+            default: k_dslash_lp_site<S, EPI_DOT_TS, MB><<<(int)g, b, 0, c->stream>>>(a); break; \
         }
+        if (variant == 3) {
+            GS_SITE_LAUNCH(6)
+        } else if (variant == 4) {
+            GS_SITE_LAUNCH(8)
+        } else {
+            GS_SITE_LAUNCH(4)
+        }
+#undef GS_SITE_LAUNCH
     }
     ++*launches;
     GS_CHECK_LAUNCH(c);
@@ -947,7 +959,8 @@ struct LpPlanData {
     int64_t nb = 0;        // labels below nb are excluded (0 for the full lattice)
     int64_t n = 0;         // sites of the set
     long long hops = 0;    // in-set neighbour terms of one D application
-    int variant = 0;       // stencil variant: 1 = thread per site, 2 = warp per direction
+    int variant = 0;       // stencil variant: 1/3/4 = thread per site (register budget for
+                           // 4/6/8 blocks per SM), 2 = warp per direction
     int2* nbr_r = nullptr;
     void* links = nullptr;
 };
@@ -1054,7 +1067,7 @@ static gs_status lp_tune(gs_ctx* c, LpPlanData& pd) {
     float best = 0.f;
     const bool was_on = c->prof.on;
     c->prof.on = false;
-    for (int v = 1; v <= 2; ++v) {
+    for (int v = 1; v <= 4; ++v) {
         long long l = 0;
         for (int r = 0; r < 7; ++r) {
             if (r == 2) GS_CUDA(c, cudaEventRecord(e0, c->stream));
