@@ -206,12 +206,17 @@ def run_reference(args, rank, world):
 
 def kernel_case(args):
     """One kernel on a large lattice: `reps` launches timed with CUDA events."""
+    dims = tuple(int(v) for v in args.dims.split(","))
+    out = stencil_roofline(args.case, dims, args.prec, args.variant, args.reps)
+    print(json.dumps(out), flush=True)
+
+
+def stencil_roofline(case, dims, prec_name="f32", variant=0, reps=20):
     import torch
     import __graft_entry__ as g
     g.build()
     import paper_0704_2341_gb300 as gs
     import lattice_inputs as li
-    dims = tuple(int(v) for v in args.dims.split(","))
     V = li.volume(dims)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
@@ -223,12 +228,12 @@ def kernel_case(args):
     ctx.set_gauge(U)
     x = torch.randn(V, 4, 3, dtype=torch.complex128, device=dev)
     y = torch.empty_like(x)
-    if args.case == "wilson_f64":
+    if case == "wilson_f64":
         prec = gs.GS_F64
         run = lambda: ctx.wilson_apply(x, y)   # noqa: E731
     else:
-        prec = gs.GS_F32 if args.prec == "f32" else gs.GS_BF16
-        ctx.set_option(gs.GS_OPT_STENCIL_VARIANT, args.variant)
+        prec = gs.GS_F32 if prec_name == "f32" else gs.GS_BF16
+        ctx.set_option(gs.GS_OPT_STENCIL_VARIANT, variant)
         xl = torch.empty(gs.lowp_bytes(V, prec), dtype=torch.uint8, device=dev)
         yl = torch.empty_like(xl)
         ctx.lowp_pack(0, 0, 0, prec, x, xl)
@@ -237,14 +242,14 @@ def kernel_case(args):
     for _ in range(3):
         run()
     ctx.profile(True)
-    for _ in range(args.reps):
+    for _ in range(reps):
         run()
     p = ctx.profile_read(prec)
     ctx.profile(False)
     ms = p.ms / p.launches
     peaks = _peaks()
-    out = {"case": args.case, "prec": args.prec if args.case != "wilson_f64" else "f64",
-           "variant": ctx.get_option(gs.GS_OPT_STENCIL_VARIANT) if args.case != "wilson_f64" else None,
+    out = {"case": case, "prec": prec_name if case != "wilson_f64" else "f64",
+           "variant": ctx.get_option(gs.GS_OPT_STENCIL_VARIANT) if case != "wilson_f64" else None,
            "dims": dims, "sites": V, "launches": p.launches,
            "us_per_launch": 1e3 * ms, "sites_per_s": V / (ms / 1e3),
            "tflops": p.flops / p.launches / (ms / 1e3) / 1e12,
@@ -253,8 +258,10 @@ def kernel_case(args):
            "frac_hbm": (p.bytes / p.launches / (ms / 1e3) / 1e9 / peaks["hbm_gbs"])
            if peaks.get("hbm_gbs") else None,
            "algorithmic_bytes_per_launch": p.bytes / p.launches}
-    print(json.dumps(out), flush=True)
     ctx.close()
+    del x, y
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -264,6 +271,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-lowp-dslash", action="store_true",
+                    help="skip the 32^3x64 low-precision stencil roofline")
     ap.add_argument("--_cpu-sample", action="store_true", dest="cpu_sample")
     ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp"],
                     help="kernel micro-benchmark instead of the solve (for profiling)")
@@ -379,6 +388,27 @@ def main():
         e2e_ms += a.elapsed_time(b)
     barrier()
 
+    # the same workload with the mixed-precision inner solve (same tolerances)
+    mixed = {}
+    for name, prec in (("f32", gs.GS_F32), ("bf16", gs.GS_BF16)):
+        o = gs.gs_default_opts(inner_prec=prec)
+        for _ in range(2):
+            for (t, mu, inv) in PERMS:
+                ctx.schur_solve(t, mu, inv, f, x, o)
+        mms, mworst = 0.0, 0.0
+        barrier()
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for (t, mu, inv) in PERMS:
+                st = ctx.schur_solve(t, mu, inv, f, x, o)
+                mworst = max(mworst, st.true_residual)
+            b.record(stream)
+            b.synchronize()
+            mms += a.elapsed_time(b)
+        mixed[name] = {"value": len(PERMS) * args.steps / (mms / 1e3), "unit": UNIT,
+                       "ms_per_step": mms / args.steps, "max_true_residual": mworst}
     if dist is not None:
         tt = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -430,10 +460,25 @@ def main():
                 "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in x_host)},
         "clocks": clock_info,
     }
+    for name in mixed:
+        mixed[name]["speedup_vs_plain_f64"] = mixed[name]["value"] / value
+    line["mixed_inner"] = mixed
+    if not args.no_lowp_dslash:
+        ctx.close()
+        ctx = None
+        torch.cuda.empty_cache()
+        lowp = {}
+        for pn in ("f32", "bf16"):
+            r = stencil_roofline("wilson_lp", (32, 32, 32, 64), pn, 0, 20)
+            lowp[pn] = {"gbs": r["gbs"], "frac_of_measured_hbm": r["frac_hbm"],
+                        "us_per_launch": r["us_per_launch"], "variant": r["variant"],
+                        "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"]}
+        line["dslash_lowp_32x32x32x64"] = lowp
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(0)
     print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 
