@@ -128,7 +128,11 @@ gs_status gs_set_gauge(gs_ctx* ctx, const void* U_dev);
  * direction (four partial sums combined in shared memory).  gs_get_option
  * returns the forced value, or under autotuning the variant chosen most
  * recently. */
-enum { GS_OPT_STENCIL_VARIANT = 1 };
+enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2 };
+/* GS_OPT_INNER_KERNEL: 0 = each inner BiCGStab solve runs as one persistent
+ * cooperative kernel (grid barriers with bounded waits between its phases;
+ * the default), 1 = five kernel launches per iteration with the convergence
+ * flag read back while iterations are queued. */
 gs_status gs_set_option(gs_ctx* ctx, int option, int value);
 gs_status gs_get_option(gs_ctx* ctx, int option, int* value);
 
@@ -221,10 +225,15 @@ typedef struct {
 } gs_kernel_profile;
 
 gs_status gs_profile(gs_ctx* ctx, int enable);
-/* prec selects the stencil family: GS_F64 (k_dslash_f64), GS_F32 or GS_BF16
- * (the low-precision stencil; bytes use 96 / 48 B per spinor and 48 / 24 B
- * per 12-real link). */
-gs_status gs_profile_read(gs_ctx* ctx, int prec, gs_kernel_profile* out);
+/* family: GS_PROF_STENCIL_F64 (k_dslash_f64), GS_PROF_STENCIL_F32 /
+ * GS_PROF_STENCIL_BF16 (the low-precision stencil; bytes use 96 / 48 B per
+ * spinor and 48 / 24 B per 12-real link), GS_PROF_SOLVER_F64 /
+ * GS_PROF_SOLVER_LP (the persistent BiCGStab kernels: per launch, two D_rr
+ * applications and 84 flop per complex entry of vector updates per
+ * iteration; "sites" counts stencil output sites). */
+enum { GS_PROF_STENCIL_F64 = 0, GS_PROF_STENCIL_F32 = 1, GS_PROF_STENCIL_BF16 = 2,
+       GS_PROF_SOLVER_F64 = 3, GS_PROF_SOLVER_LP = 4 };
+gs_status gs_profile_read(gs_ctx* ctx, int family, gs_kernel_profile* out);
 
 /* Low-precision vectors and stencil: the arithmetic of the mixed inner solve
  * (GS_F32 / GS_BF16 storage, FP32 arithmetic, links stored as two rows of

@@ -21,7 +21,9 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOMEM", 3: "GS_MAXITER",
 GS_TYPE_I, GS_TYPE_II = 1, 2
 GS_F64, GS_F32, GS_BF16 = 0, 1, 2
 GS_GMRES, GS_BICGSTAB = 0, 1
-GS_OPT_STENCIL_VARIANT = 1
+GS_OPT_STENCIL_VARIANT, GS_OPT_INNER_KERNEL = 1, 2
+GS_PROF_STENCIL_F64, GS_PROF_STENCIL_F32, GS_PROF_STENCIL_BF16, GS_PROF_SOLVER_F64, \
+    GS_PROF_SOLVER_LP = range(5)
 
 # every symbol the header declares
 EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson_apply",

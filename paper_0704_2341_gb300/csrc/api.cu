@@ -112,6 +112,7 @@ gs_status gs_destroy(gs_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     free_mixed(c);
+    free_persist(c);
     for (Plan* p : c->plans) free_plan(p);
     c->plans.clear();
     cudaFree(c->U_abi);
@@ -162,6 +163,11 @@ gs_status gs_set_option(gs_ctx* c, int option, int value) {
         invalidate_mixed_links(c);  // re-tune / re-select on next use
         return GS_OK;
     }
+    if (option == GS_OPT_INNER_KERNEL) {
+        if (value < 0 || value > 1) return set_err(c, GS_EINVAL, "inner kernel %d not in 0..1", value);
+        c->opt_inner_kernel = value;
+        return GS_OK;
+    }
     return set_err(c, GS_EINVAL, "unknown option %d", option);
 }
 
@@ -169,6 +175,10 @@ gs_status gs_get_option(gs_ctx* c, int option, int* value) {
     if (!c || !value) return GS_EINVAL;
     if (option == GS_OPT_STENCIL_VARIANT) {
         *value = c->opt_stencil_variant ? c->opt_stencil_variant : c->tuned_variant;
+        return GS_OK;
+    }
+    if (option == GS_OPT_INNER_KERNEL) {
+        *value = c->opt_inner_kernel;
         return GS_OK;
     }
     return set_err(c, GS_EINVAL, "unknown option %d", option);

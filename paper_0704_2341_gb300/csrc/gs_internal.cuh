@@ -128,7 +128,7 @@ struct Profiler {
     std::vector<Pending> pending;
     int* ran_dev = nullptr;           // per slot: 1 if the launch did work (not an early exit)
     int* ran_host = nullptr;          // pinned
-    gs_kernel_profile tot[3] = {};    // by stencil precision
+    gs_kernel_profile tot[5] = {};    // stencil F64/F32/BF16, persistent solver F64 / low precision
 };
 constexpr int kProfSlots = 2048;
 
@@ -195,6 +195,8 @@ struct gs_ctx {
     gs::Profiler prof;
     void* mixed = nullptr;             // mixed-precision state (mixed.cu)
     int opt_stencil_variant = 0;       // 0 = autotune, 1/3/4 = site (4/6/8 blocks), 2 = direction
+    int opt_inner_kernel = 0;          // 0 = persistent cooperative BiCGStab, 1 = one launch per phase
+    void* persist = nullptr;           // persistent-solver scratch (persistent.cu)
     int tuned_variant = 0;             // the variant the autotuner picked last
     std::string err;
 };
@@ -287,6 +289,10 @@ gs_status inner_solve_f64(gs_ctx* c, const Plan* p, const double2* t, double2* z
 gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2* z,
                             const gs_solve_opts& o, gs_solve_stats& st);
 void free_mixed(gs_ctx* c);
+void free_persist(gs_ctx* c);
+gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs& C,
+                              const double2* b, double2* x, InnerWork& w, int64_t n, double tol,
+                              int maxit);
 void invalidate_mixed_links(gs_ctx* c);
 gs_status schur_apply_internal(gs_ctx* c, const Plan* p, const double2* xb, double2* yb,
                                const gs_solve_opts& o, gs_solve_stats& st);

@@ -139,7 +139,8 @@ gs_status inner_solve_f64(gs_ctx* c, const Plan* p, const double2* t, double2* z
     gs_status s = ensure_inner(c, nr);
     if (s != GS_OK) return s;
     InnerWork& w = c->inner;
-    if ((s = launch_bicg_init(c, w, t, z, n, o.inner_tol)) != GS_OK) return s;
+    if (c->opt_inner_kernel != 0 && (s = launch_bicg_init(c, w, t, z, n, o.inner_tol)) != GS_OK)
+        return s;
 
     StencilArgs k1 = rr_args(c, p, w.v, w.p);
     k1.epi = EPI_DOT_RHAT_V;
@@ -152,29 +153,54 @@ gs_status inner_solve_f64(gs_ctx* c, const Plan* p, const double2* t, double2* z
     k3.st = w.st;
     k3.red = w.red;
 
-    // Iterations are queued ahead of the GPU; the host waits on the event of
-    // the iteration `depth` behind and reads the mapped `done` flag, so at most
-    // `depth` no-op iterations are queued after convergence.
-    const int depth = (o.check_every >= 1 && o.check_every <= 4) ? o.check_every : 2;
     volatile BicgPublic* pub = w.pub_host;
-    int enq = 0;
-    GS_CUDA(c, cudaEventRecord(w.ev[0], c->stream));  // after init
-    GS_CUDA(c, cudaEventSynchronize(w.ev[0]));
-    if (!pub->done) {
-        for (int it = 0; it < o.inner_max_iter; ++it) {
-            if (it >= depth) {
-                GS_CUDA(c, cudaEventSynchronize(w.ev[(it - depth) % 4]));
-                if (pub->done) break;
-            }
-            if ((s = launch_stencil_f64(c, k1)) != GS_OK) return s;
-            if ((s = launch_bicg_s_update(c, w, z, n)) != GS_OK) return s;
-            if ((s = launch_stencil_f64(c, k3)) != GS_OK) return s;
-            if ((s = launch_bicg_xr_update(c, w, z, n)) != GS_OK) return s;
-            if ((s = launch_bicg_p_update(c, w, n)) != GS_OK) return s;
-            GS_CUDA(c, cudaEventRecord(w.ev[it % 4], c->stream));
-            enq = it + 1;
+    if (c->opt_inner_kernel == 0) {
+        // the whole solve in one cooperative launch (persistent.cu)
+        int slot = -1;
+        if (c->prof.on && (s = prof_begin(c, &slot)) != GS_OK) return s;
+        s = persistent_bicg_f64(c, k1, k3, t, z, w, n, o.inner_tol, o.inner_max_iter);
+        if (s != GS_OK) return s;
+        if (slot >= 0) GS_CUDA(c, cudaEventRecord(c->prof.ev[2 * slot + 1], c->stream));
+        GS_CUDA(c, cudaEventRecord(w.ev[0], c->stream));
+        GS_CUDA(c, cudaEventSynchronize(w.ev[0]));
+        if (slot >= 0) {
+            // algorithmic FP64 work: two D_rr applications per iteration and the
+            // vector updates (84 flop per complex entry per iteration)
+            long long hops;
+            double fl, by;
+            stencil_work(c, p, k1, &hops, &fl, &by);
+            const double it = (double)pub->iter;
+            c->prof.ran_host[slot] = 1;
+            GS_CUDA(c, cudaMemcpy(c->prof.ran_dev + slot, c->prof.ran_host + slot, sizeof(int),
+                                  cudaMemcpyHostToDevice));
+            c->prof.pending.push_back(
+                {slot, 3, (long long)(2 * it * nr), (long long)(2 * it * hops),
+                 it * (2.0 * fl + 84.0 * (double)n), it * (2.0 * by + 14.0 * 16.0 * (double)n)});
         }
-        if (enq > 0) GS_CUDA(c, cudaEventSynchronize(w.ev[(enq - 1) % 4]));
+    } else {
+        // Iterations are queued ahead of the GPU; the host waits on the event of
+        // the iteration `depth` behind and reads the mapped `done` flag, so at most
+        // `depth` no-op iterations are queued after convergence.
+        const int depth = (o.check_every >= 1 && o.check_every <= 4) ? o.check_every : 2;
+        int enq = 0;
+        GS_CUDA(c, cudaEventRecord(w.ev[0], c->stream));  // after init
+        GS_CUDA(c, cudaEventSynchronize(w.ev[0]));
+        if (!pub->done) {
+            for (int it = 0; it < o.inner_max_iter; ++it) {
+                if (it >= depth) {
+                    GS_CUDA(c, cudaEventSynchronize(w.ev[(it - depth) % 4]));
+                    if (pub->done) break;
+                }
+                if ((s = launch_stencil_f64(c, k1)) != GS_OK) return s;
+                if ((s = launch_bicg_s_update(c, w, z, n)) != GS_OK) return s;
+                if ((s = launch_stencil_f64(c, k3)) != GS_OK) return s;
+                if ((s = launch_bicg_xr_update(c, w, z, n)) != GS_OK) return s;
+                if ((s = launch_bicg_p_update(c, w, n)) != GS_OK) return s;
+                GS_CUDA(c, cudaEventRecord(w.ev[it % 4], c->stream));
+                enq = it + 1;
+            }
+            if (enq > 0) GS_CUDA(c, cudaEventSynchronize(w.ev[(enq - 1) % 4]));
+        }
     }
     const int iters = pub->iter;
     const double rel = pub->bb > 0.0 ? sqrt(pub->rr / pub->bb) : 0.0;

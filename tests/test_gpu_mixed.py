@@ -28,13 +28,15 @@ def _ctx(gs, torch, dims, m0, U):
     return ctx
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 @pytest.mark.parametrize("t,mu,inv", TYPES)
-def test_mixed_schur_apply_matches_oracle(env, prec, t, mu, inv):
+def test_mixed_schur_apply_matches_oracle(env, prec, t, mu, inv, kernel):
     torch, gs = env
     dims, m0 = (4, 4, 4, 4), 0.2
     U = li.random_gauge(dims, 0.3, 0)
     ctx = _ctx(gs, torch, dims, m0, U)
+    ctx.set_option(gs.GS_OPT_INNER_KERNEL, kernel)
     perm, nb = permute.permutation(dims, t, mu, inv)
     xb = li.gaussian_source(dims, 100).reshape(-1, 12)[perm[:nb]].ravel()
     xbd = to_dev(xb, torch)

@@ -82,8 +82,9 @@ def test_wilson_apply_matches_oracle(env, dims, eps, m0):
     ctx.close()
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("t,mu,inv", TYPES + [(2, 3, False), (2, 1, True)])
-def test_schur_apply_matches_oracle_4x4(env, t, mu, inv):
+def test_schur_apply_matches_oracle_4x4(env, t, mu, inv, kernel):
     """4^4, exp(i 0.3 H) seed 0, m0 = 0.2, Gaussian source seed 100 (the small
     workload), inner tolerance 1e-14: S_bb x_b within 1e-12 of the oracle
     (direct sparse LU for D_rr^-1)."""
@@ -91,6 +92,7 @@ def test_schur_apply_matches_oracle_4x4(env, t, mu, inv):
     dims, m0 = (4, 4, 4, 4), 0.2
     U = li.random_gauge(dims, 0.3, 0)
     ctx = _ctx(gs, torch, dims, m0, U)
+    ctx.set_option(gs.GS_OPT_INNER_KERNEL, kernel)   # persistent / one launch per phase
     perm, nb = permute.permutation(dims, t, mu, inv)
     src = li.gaussian_source(dims, 100).reshape(-1, 12)
     xb = src[perm[:nb]].ravel()
@@ -206,14 +208,16 @@ def _cfg1_field():
     return _CFG1["dims"], _CFG1["U"], _CFG1["D"]
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("t,mu,inv", TYPES)
-def test_schur_solve_8x4_heatbath_residual(env, t, mu, inv):
+def test_schur_solve_8x4_heatbath_residual(env, t, mu, inv, kernel):
     """The benchmark workload: 8^4 plaquette-action field at beta = 5.4,
     m0 = -0.4, GMRES(30) to 1e-10 with back-substitution.  The GPU solution
     must solve the oracle's own D: ||f - D x|| / ||f|| <= 1e-10."""
     torch, gs = env
     dims, U, D = _cfg1_field()
     ctx = _ctx(gs, torch, dims, -0.4, U)
+    ctx.set_option(gs.GS_OPT_INNER_KERNEL, kernel)
     f = li.gaussian_source(dims, 100)
     fd = to_dev(f, torch)
     xd = torch.empty_like(fd)
