@@ -88,6 +88,10 @@ typedef struct {
     int    check_every;    /* inner iterations queued ahead of the convergence read-back, 1..4 [2] */
     double lowp_tol;       /* relative tolerance of each low-precision solve; 0 = 1e-5
                             * for GS_F32, 3e-2 for GS_BF16 [0] */
+    int    inner_relax;    /* outer GMRES: relax the inner tolerance of Arnoldi step j to
+                            * inner_tol * ||w_b|| / ||r_j|| (at most relax_cap), accepting
+                            * the solve only on a tightly recomputed true residual [1] */
+    double relax_cap;      /* largest relaxed inner tolerance [1e-4] */
 } gs_solve_opts;
 
 /* Statistics written by schur_apply / schur_solve (may be NULL). */

@@ -38,7 +38,8 @@ class gs_solve_opts(ctypes.Structure):
                 ("restart", ctypes.c_int), ("outer_solver", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("inner_max_iter", ctypes.c_int),
                 ("inner_prec", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("lowp_tol", ctypes.c_double)]
+                ("lowp_tol", ctypes.c_double), ("inner_relax", ctypes.c_int),
+                ("relax_cap", ctypes.c_double)]
 
 
 class gs_solve_stats(ctypes.Structure):

@@ -25,6 +25,8 @@ gs_status check_opts(gs_ctx* c, const gs_solve_opts& o) {
         return set_err(c, GS_EINVAL, "unknown inner precision %d", o.inner_prec);
     if (!(o.lowp_tol >= 0.0) || o.lowp_tol >= 1.0)
         return set_err(c, GS_EINVAL, "lowp_tol must be in [0, 1)");
+    if (o.inner_relax && (!(o.relax_cap > 0.0) || o.relax_cap >= 1.0))
+        return set_err(c, GS_EINVAL, "relax_cap must be in (0, 1)");
     return GS_OK;
 }
 
@@ -53,6 +55,8 @@ void gs_default_opts(gs_solve_opts* o) {
     o->inner_prec = GS_F64;
     o->check_every = 2;
     o->lowp_tol = 0.0;
+    o->inner_relax = 1;
+    o->relax_cap = 1e-4;
 }
 
 const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "null context"; }

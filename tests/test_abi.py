@@ -39,6 +39,7 @@ def test_calls_without_gpu_fail_cleanly():
         gs.gs_create((4, 4, 4, 4), 0.1)
     o = gs.gs_default_opts()
     assert o.tol == 1e-10 and o.restart == 30 and o.inner_tol == 1e-12
+    assert o.inner_relax == 1 and o.relax_cap == 1e-4
 
 
 def test_oracle_and_product_are_independent():

@@ -244,3 +244,28 @@ def test_schur_solve_8x4_matches_oracle_solution(env):
     # both residuals <= 1e-10: the solutions agree to kappa(D) * 2e-10
     assert rel(xd.cpu().numpy(), xo) <= 1e-7
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_relaxed_inner_tolerance_same_solution_fewer_iterations(env, prec):
+    """Inexact Krylov on the 8^4 workload: relaxing the inner tolerance of
+    later Arnoldi steps keeps the 1e-10 true residual (checked with the
+    oracle's D) and the solution, with fewer inner iterations."""
+    torch, gs = env
+    dims, U, D = _cfg1_field()
+    ctx = _ctx(gs, torch, dims, -0.4, U)
+    f = li.gaussian_source(dims, 100)
+    fd = to_dev(f, torch)
+    xs = []
+    its = []
+    for relax in (0, 1):
+        xd = torch.empty_like(fd)
+        st = ctx.schur_solve(2, 0, 1, fd, xd,
+                             gs.gs_default_opts(inner_relax=relax, inner_prec=prec))
+        x = xd.cpu().numpy().ravel()
+        assert np.linalg.norm(f.ravel() - D @ x) <= 1e-10 * np.linalg.norm(f)
+        xs.append(x)
+        its.append(st.inner_iters)
+    assert rel(xs[1], xs[0]) <= 1e-7
+    assert its[1] < its[0]
+    ctx.close()
