@@ -260,6 +260,42 @@ gs_status gs_lowp_unpack(gs_ctx* ctx, int type, int dir, int inverse, int prec,
 gs_status wilson_apply_lowp(gs_ctx* ctx, int type, int dir, int inverse, int prec,
                             const void* x_lp_dev, void* y_lp_dev);
 
+/* Several sources on one lattice (nrhs = 1..32), solved together: the
+ * block UL solve of schur_solve for every source, with the inner D_rr solves
+ * of all sources in one persistent low-precision kernel (opts->inner_prec
+ * must be GS_F32 or GS_BF16; FP64 defect correction as in schur_solve) and the
+ * outer GMRES(m) systems advanced in lock step (one batched S_bb
+ * application per Arnoldi step).  f_dev, x_dev: complex128
+ * [nrhs][V][4][3], site order.  stats (may be NULL) aggregates: iterations
+ * summed, true_residual and outer_residual the worst over the sources.
+ * Synchronises the stream. */
+gs_status schur_solve_multi(gs_ctx* ctx, int type, int dir, int inverse, int nrhs,
+                            const void* f_dev, void* x_dev, const gs_solve_opts* opts,
+                            gs_solve_stats* stats);
+
+/* Several problems -- lattices with their own contexts, permutations and
+ * source counts -- solved concurrently: problem i is schur_solve_multi on
+ * ctxs[i] (its own stream) with type[i], dir[i], inverse[i], nrhs[i],
+ * f_dev[i], x_dev[i]; each problem's persistent kernels get a share of the
+ * SMs proportional to V x nrhs.  The contexts must be distinct.  stats (may
+ * be NULL) is an array of nprob entries.  Returns the worst status. */
+gs_status schur_solve_batched(int nprob, gs_ctx* const* ctxs, const int* type, const int* dir,
+                              const int* inverse, const int* nrhs, const void* const* f_dev,
+                              void* const* x_dev, const gs_solve_opts* opts,
+                              gs_solve_stats* stats);
+
+/* Low-precision vectors of nrhs sources (1..32) with the sources interleaved
+ * inside each site: GS_F32 float [6][n][nrhs][4], GS_BF16 bf16
+ * [3][n][nrhs][8] (n as for gs_lowp_pack); the complex128 side is
+ * [nrhs][n][4][3].  wilson_apply_lowp_multi applies D (type 0) or D_rr to all
+ * sources at once, reading each site's links once per launch.  Asynchronous. */
+gs_status gs_lowp_pack_multi(gs_ctx* ctx, int type, int dir, int inverse, int prec, int nrhs,
+                             const void* x_dev, void* x_lp_dev);
+gs_status gs_lowp_unpack_multi(gs_ctx* ctx, int type, int dir, int inverse, int prec, int nrhs,
+                               const void* x_lp_dev, void* x_dev);
+gs_status wilson_apply_lowp_multi(gs_ctx* ctx, int type, int dir, int inverse, int prec,
+                                  int nrhs, const void* x_lp_dev, void* y_lp_dev);
+
 /* Text of the last error on this context ("" if none).  The pointer stays
  * valid until the next call on the context. */
 const char* gs_last_error(const gs_ctx* ctx);

@@ -17,5 +17,7 @@ __all__ = ["Context", "GschurError", "gs_create", "gs_destroy", "gs_set_gauge",
            "gs_lowp_unpack", "wilson_apply_lowp", "lowp_bytes", "gs_set_option",
            "gs_get_option", "GS_OPT_STENCIL_VARIANT", "GS_OPT_INNER_KERNEL", "GS_PROF_STENCIL_F64",
            "GS_PROF_STENCIL_F32", "GS_PROF_STENCIL_BF16", "GS_PROF_SOLVER_F64", "GS_PROF_SOLVER_LP",
+           "schur_solve_multi", "schur_solve_batched", "gs_lowp_pack_multi", "gs_lowp_unpack_multi",
+           "wilson_apply_lowp_multi",
            "GS_TYPE_I", "GS_TYPE_II", "GS_F64", "GS_F32", "GS_BF16", "GS_GMRES",
            "GS_BICGSTAB", "GS_OK", "GS_MAXITER"]

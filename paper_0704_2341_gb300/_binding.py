@@ -30,7 +30,8 @@ EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson
            "permute_sites", "gs_get_permutation", "schur_apply", "schur_solve",
            "gs_last_error", "gs_version", "gs_profile", "gs_profile_read",
            "wilson_apply_noalloc", "gs_lowp_pack", "gs_lowp_unpack", "wilson_apply_lowp", "gs_set_option",
-           "gs_get_option")
+           "gs_get_option", "schur_solve_multi", "schur_solve_batched", "gs_lowp_pack_multi",
+           "gs_lowp_unpack_multi", "wilson_apply_lowp_multi")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -90,6 +91,16 @@ def _load():
         "gs_profile_read": (i32, [vp, i32, ctypes.POINTER(gs_kernel_profile)]),
         "gs_lowp_pack": (i32, [vp, i32, i32, i32, i32, vp, vp]),
         "gs_set_option": (i32, [vp, i32, i32]),
+        "schur_solve_multi": (i32, [vp, i32, i32, i32, i32, vp, vp, ctypes.POINTER(gs_solve_opts),
+                                    ctypes.POINTER(gs_solve_stats)]),
+        "schur_solve_batched": (i32, [i32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp),
+                                      ctypes.POINTER(vp), ctypes.POINTER(gs_solve_opts),
+                                      ctypes.POINTER(gs_solve_stats)]),
+        "gs_lowp_pack_multi": (i32, [vp, i32, i32, i32, i32, i32, vp, vp]),
+        "gs_lowp_unpack_multi": (i32, [vp, i32, i32, i32, i32, i32, vp, vp]),
+        "wilson_apply_lowp_multi": (i32, [vp, i32, i32, i32, i32, i32, vp, vp]),
         "gs_get_option": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int)]),
         "gs_lowp_unpack": (i32, [vp, i32, i32, i32, i32, vp, vp]),
         "wilson_apply_lowp": (i32, [vp, i32, i32, i32, i32, vp, vp]),
@@ -215,6 +226,48 @@ def gs_profile_read(ctx, prec=GS_F64):
     return out
 
 
+def schur_solve_multi(ctx, ptype, dir, inverse, nrhs, f, x, opts=None, allow=(GS_OK,)):
+    o = opts if opts is not None else gs_default_opts(inner_prec=GS_F32)
+    st = gs_solve_stats()
+    _check(ctx, lib.schur_solve_multi(ctx, ptype, dir, int(bool(inverse)), nrhs, _ptr(f), _ptr(x),
+                                      ctypes.byref(o), ctypes.byref(st)), allow)
+    return st
+
+
+def schur_solve_batched(problems, opts=None):
+    """problems: list of dicts with keys ctx (handle), type, dir, inverse, nrhs, f, x.
+    Returns (status, [gs_solve_stats])."""
+    n = len(problems)
+    o = opts if opts is not None else gs_default_opts(inner_prec=GS_F32)
+    VP = ctypes.c_void_p
+    IA = ctypes.c_int * n
+    ctxs = (VP * n)(*[p["ctx"] for p in problems])
+    ty = IA(*[p["type"] for p in problems])
+    di = IA(*[p.get("dir", 0) for p in problems])
+    iv = IA(*[int(bool(p.get("inverse", 0))) for p in problems])
+    nr = IA(*[p["nrhs"] for p in problems])
+    fs = (VP * n)(*[_ptr(p["f"]) for p in problems])
+    xs = (VP * n)(*[_ptr(p["x"]) for p in problems])
+    sts = (gs_solve_stats * n)()
+    status = lib.schur_solve_batched(n, ctxs, ty, di, iv, nr, fs, xs, ctypes.byref(o), sts)
+    return status, list(sts)
+
+
+def gs_lowp_pack_multi(ctx, ptype, dir, inverse, prec, nrhs, x, x_lp):
+    return _check(ctx, lib.gs_lowp_pack_multi(ctx, ptype, dir, int(bool(inverse)), prec, nrhs,
+                                              _ptr(x), _ptr(x_lp)))
+
+
+def gs_lowp_unpack_multi(ctx, ptype, dir, inverse, prec, nrhs, x_lp, x):
+    return _check(ctx, lib.gs_lowp_unpack_multi(ctx, ptype, dir, int(bool(inverse)), prec, nrhs,
+                                                _ptr(x_lp), _ptr(x)))
+
+
+def wilson_apply_lowp_multi(ctx, ptype, dir, inverse, prec, nrhs, x_lp, y_lp):
+    return _check(ctx, lib.wilson_apply_lowp_multi(ctx, ptype, dir, int(bool(inverse)), prec, nrhs,
+                                                   _ptr(x_lp), _ptr(y_lp)))
+
+
 def gs_set_option(ctx, option, value):
     return _check(ctx, lib.gs_set_option(ctx, option, value))
 
@@ -287,6 +340,18 @@ class Context:
 
     def schur_solve(self, ptype, dir, inverse, f, x, opts=None, allow=(GS_OK,)):
         return schur_solve(self.handle, ptype, dir, inverse, f, x, opts, allow)
+
+    def schur_solve_multi(self, ptype, dir, inverse, nrhs, f, x, opts=None, allow=(GS_OK,)):
+        return schur_solve_multi(self.handle, ptype, dir, inverse, nrhs, f, x, opts, allow)
+
+    def lowp_pack_multi(self, ptype, dir, inverse, prec, nrhs, x, x_lp):
+        return gs_lowp_pack_multi(self.handle, ptype, dir, inverse, prec, nrhs, x, x_lp)
+
+    def lowp_unpack_multi(self, ptype, dir, inverse, prec, nrhs, x_lp, x):
+        return gs_lowp_unpack_multi(self.handle, ptype, dir, inverse, prec, nrhs, x_lp, x)
+
+    def wilson_apply_lowp_multi(self, ptype, dir, inverse, prec, nrhs, x_lp, y_lp):
+        return wilson_apply_lowp_multi(self.handle, ptype, dir, inverse, prec, nrhs, x_lp, y_lp)
 
     def profile(self, enable):
         return gs_profile(self.handle, enable)

@@ -115,6 +115,7 @@ gs_status gs_destroy(gs_ctx* c) {
     if (!c) return GS_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    free_multi(c);
     free_mixed(c);
     free_persist(c);
     for (Plan* p : c->plans) free_plan(p);

@@ -1,0 +1,59 @@
+// Grid-wide barrier with bounded waits for cooperative (co-resident) grids,
+// shared by the persistent solver kernels.
+#pragma once
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr long long kSpinLimit = 16000000;
+struct GridSync {
+    unsigned int* count;
+    unsigned int* gen;
+    int* err;
+};
+
+__device__ __forceinline__ unsigned int vload(const unsigned int* p) {
+    return *(const volatile unsigned int*)p;
+}
+__device__ __forceinline__ int vload(const int* p) { return *(const volatile int*)p; }
+
+// Returns false (in every thread of the block) if a barrier timed out.
+__device__ bool grid_sync(const GridSync& g) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int my_gen = vload(g.gen);
+        __threadfence();
+        const unsigned int arrived = atomicAdd(g.count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(g.count, 0u);
+            __threadfence();
+            atomicAdd(g.gen, 1u);
+        } else {
+            long long spins = 0;
+            while (vload(g.gen) == my_gen) {
+                if (vload(g.err) != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (++spins > kSpinLimit) {
+                    atomicExch(g.err, (int)GS_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (vload(g.err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace
+}  // namespace gs

@@ -197,6 +197,8 @@ struct gs_ctx {
     int opt_stencil_variant = 0;       // 0 = autotune, 1/3/4 = site (4/6/8 blocks), 2 = direction
     int opt_inner_kernel = 0;          // 0 = persistent cooperative BiCGStab, 1 = one launch per phase
     void* persist = nullptr;           // persistent-solver scratch (persistent.cu)
+    void* multi = nullptr;             // multi-RHS workspaces (multi.cu)
+    int coop_block_cap = 0;            // cap on cooperative grids (0 = whole GPU; batched solves)
     int tuned_variant = 0;             // the variant the autotuner picked last
     std::string err;
 };
@@ -289,6 +291,15 @@ gs_status inner_solve_f64(gs_ctx* c, const Plan* p, const double2* t, double2* z
 gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2* z,
                             const gs_solve_opts& o, gs_solve_stats& st);
 void free_mixed(gs_ctx* c);
+// low-precision tables of a set (compact neighbour table, 12-real links)
+struct LowpTables {
+    const int2* nbr;
+    const void* links;
+    int64_t n, nb;
+    long long hops;
+};
+gs_status lowp_tables(gs_ctx* c, const Plan* p, int prec, LowpTables* out);
+void free_multi(gs_ctx* c);
 void free_persist(gs_ctx* c);
 gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs& C,
                               const double2* b, double2* x, InnerWork& w, int64_t n, double tol,

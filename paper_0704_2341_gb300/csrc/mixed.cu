@@ -514,6 +514,19 @@ static gs_status lp_plan(gs_ctx* c, const Plan* p, int prec, LpPlanData** out) {
     return GS_OK;
 }
 
+gs_status lowp_tables(gs_ctx* c, const Plan* p, int prec, LowpTables* out) {
+    gs_status s = ensure_lp(c, prec, c->V - ((p->type == 0) ? 0 : p->nb));
+    if (s != GS_OK) return s;
+    LpPlanData* pd = nullptr;
+    if ((s = lp_plan(c, p, prec, &pd)) != GS_OK) return s;
+    out->nbr = pd->nbr_r;
+    out->links = pd->links;
+    out->n = pd->n;
+    out->nb = pd->nb;
+    out->hops = pd->hops;
+    return GS_OK;
+}
+
 void invalidate_mixed_links(gs_ctx* c) {
     MixedState* m = (MixedState*)c->mixed;
     if (!m) return;

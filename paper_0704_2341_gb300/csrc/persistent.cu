@@ -20,60 +20,13 @@
 // the read-only cache path is not coherent with writes of other blocks of
 // the same kernel.
 #include "dslash_f64.cuh"
+#include "gridsync.cuh"
 #include "lowp.cuh"
 
 namespace gs {
 namespace {
 
-constexpr long long kSpinLimit = 16000000;
 constexpr int kPThreads = 128;
-
-struct GridSync {
-    unsigned int* count;
-    unsigned int* gen;
-    int* err;
-};
-
-__device__ __forceinline__ unsigned int vload(const unsigned int* p) {
-    return *(const volatile unsigned int*)p;
-}
-__device__ __forceinline__ int vload(const int* p) { return *(const volatile int*)p; }
-
-// Returns false (in every thread of the block) if a barrier timed out.
-__device__ bool grid_sync(const GridSync& g) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned int my_gen = vload(g.gen);
-        __threadfence();
-        const unsigned int arrived = atomicAdd(g.count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(g.count, 0u);
-            __threadfence();
-            atomicAdd(g.gen, 1u);
-        } else {
-            long long spins = 0;
-            while (vload(g.gen) == my_gen) {
-                if (vload(g.err) != 0) {
-                    ok = 0;
-                    break;
-                }
-                if (++spins > kSpinLimit) {
-                    atomicExch(g.err, (int)GS_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        if (vload(g.err) != 0) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 // Sum NV values over the block (fixed tree); thread 0 gets the result.
 template <int NV, class T>
@@ -624,6 +577,7 @@ static int coop_grid(gs_ctx* c, K kernel, int64_t want) {
         return 0;
     }
     int64_t g = (int64_t)per_sm * c->num_sms;
+    if (c->coop_block_cap > 0 && g > c->coop_block_cap) g = c->coop_block_cap;
     if (want < g) g = want;
     if (g < 1) g = 1;
     if (g > kMaxRedBlocks) g = kMaxRedBlocks;

@@ -1,0 +1,140 @@
+"""Several sources and several lattices solved together (multi-source
+stencil, persistent multi-source inner solves, lock-step outer GMRES,
+concurrent batches), through the C ABI, against the FP64 oracle."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as sla
+
+import lattice_inputs as li
+from oracle import dirac, permute, schur
+from tests.gpu_util import lib, rel, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = torch_cuda()
+    return torch, lib()
+
+
+def _ctx(gs, torch, dims, m0, U, stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    ctx = gs.Context(dims, m0, s)
+    ctx.set_gauge(to_dev(U, torch))
+    return ctx
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 4e-6), ("bf16", 3e-2)])
+@pytest.mark.parametrize("nrhs", [1, 3, 12])
+@pytest.mark.parametrize("t", [0, 1])
+def test_multi_source_stencil(env, prec, tol, nrhs, t):
+    torch, gs = env
+    dims = (4, 4, 2, 4)
+    U = li.random_gauge(dims, 0.35, 4)
+    ctx = _ctx(gs, torch, dims, 0.05, U)
+    D = dirac.wilson_matrix(U, dims, 0.05)
+    if t == 0:
+        n = li.volume(dims)
+        A = D
+    else:
+        perm, nb = permute.permutation(dims, 1)
+        A = schur.partition(D, perm, nb)[3]
+        n = li.volume(dims) - nb
+    p = gs.GS_F32 if prec == "f32" else gs.GS_BF16
+    x = li.gaussian_source(dims, 9, n_src=max(nrhs, 2))[:nrhs].reshape(nrhs, -1, 12)[:, :n]
+    xd = to_dev(np.ascontiguousarray(x), torch)
+    xl = torch.empty(gs.lowp_bytes(n * nrhs, p), dtype=torch.uint8, device="cuda:0")
+    yl = torch.empty_like(xl)
+    yd = torch.empty_like(xd)
+    ctx.lowp_pack_multi(t, 0, 0, p, nrhs, xd, xl)
+    ctx.wilson_apply_lowp_multi(t, 0, 0, p, nrhs, xl, yl)
+    ctx.lowp_unpack_multi(t, 0, 0, p, nrhs, yl, yd)
+    got = yd.cpu().numpy().reshape(nrhs, -1)
+    for j in range(nrhs):
+        ref = A @ x[j].ravel()
+        assert np.abs(got[j] - ref).max() <= tol * np.abs(ref).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("t,mu,inv", [(1, 0, False), (2, 0, False), (1, 0, True), (2, 1, True)])
+def test_schur_solve_multi_matches_direct(env, prec, t, mu, inv):
+    torch, gs = env
+    dims, m0 = (4, 4, 4, 4), 0.2
+    U = li.random_gauge(dims, 0.3, 0)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    N = 3
+    f = li.gaussian_source(dims, 21, n_src=N)
+    fd = to_dev(f, torch)
+    xd = torch.empty_like(fd)
+    p = gs.GS_F32 if prec == "f32" else gs.GS_BF16
+    st = ctx.schur_solve_multi(t, mu, int(inv), N, fd, xd, gs.gs_default_opts(inner_prec=p))
+    D = dirac.wilson_matrix(U, dims, m0).tocsc()
+    x = xd.cpu().numpy().reshape(N, -1)
+    for j in range(N):
+        xs = sla.spsolve(D, f[j].ravel())
+        assert rel(x[j], xs) <= 1e-9
+    assert st.true_residual <= 1e-10
+    ctx.close()
+
+
+def test_schur_solve_multi_8x4_heatbath(env):
+    torch, gs = env
+    dims, U = li.workload_gauge("8^4 heatbath b5.4")
+    ctx = _ctx(gs, torch, dims, -0.4, U)
+    N = 4
+    f = li.gaussian_source(dims, 31, n_src=N)
+    fd = to_dev(f, torch)
+    xd = torch.empty_like(fd)
+    st = ctx.schur_solve_multi(1, 0, 0, N, fd, xd, gs.gs_default_opts(inner_prec=gs.GS_F32))
+    D = dirac.wilson_matrix(U, dims, -0.4)
+    x = xd.cpu().numpy().reshape(N, -1)
+    for j in range(N):
+        assert np.linalg.norm(f[j].ravel() - D @ x[j]) <= 1e-10 * np.linalg.norm(f[j])
+    assert st.true_residual <= 1e-10
+    ctx.close()
+
+
+def test_schur_solve_batched_concurrent_problems(env):
+    """Three problems of different lattices, permutations and source counts
+    on three contexts and streams at once, each against a direct solve."""
+    torch, gs = env
+    specs = [((4, 4, 4, 4), 0.2, 0.3, 0, 1, 0, 0, 2),
+             ((2, 2, 6, 2), 0.1, 0.4, 9, 2, 0, 1, 3),
+             ((4, 2, 4, 4), -0.1, 0.3, 5, 2, 2, 0, 1)]
+    ctxs, probs, refs, keep = [], [], [], []
+    for dims, m0, eps, seed, t, mu, inv, N in specs:
+        U = li.random_gauge(dims, eps, seed)
+        s = torch.cuda.Stream()
+        ctx = _ctx(gs, torch, dims, m0, U, s.cuda_stream)
+        f = li.gaussian_source(dims, seed + 50, n_src=max(N, 2))[:N]
+        fd = to_dev(np.ascontiguousarray(f), torch)
+        xd = torch.zeros_like(fd)
+        probs.append(dict(ctx=ctx.handle, type=t, dir=mu, inverse=inv, nrhs=N, f=fd, x=xd))
+        refs.append((dirac.wilson_matrix(U, dims, m0).tocsc(), f))
+        ctxs.append(ctx)
+        keep.append(s)
+    torch.cuda.synchronize()
+    status, stats = gs.schur_solve_batched(probs, gs.gs_default_opts(inner_prec=gs.GS_F32))
+    torch.cuda.synchronize()
+    assert status == gs.GS_OK
+    for (D, f), pr, st in zip(refs, probs, stats):
+        x = pr["x"].cpu().numpy().reshape(pr["nrhs"], -1)
+        for j in range(pr["nrhs"]):
+            assert rel(x[j], sla.spsolve(D, f[j].ravel())) <= 1e-9
+        assert st.true_residual <= 1e-10
+    for c in ctxs:
+        c.close()
+
+
+def test_multi_rejects_bad_arguments(env):
+    torch, gs = env
+    dims = (4, 4, 2, 2)
+    ctx = _ctx(gs, torch, dims, 0.1, li.random_gauge(dims, 0.3, 2))
+    z = torch.zeros(li.volume(dims) * 12, dtype=torch.complex128, device="cuda:0")
+    with pytest.raises(gs.GschurError):
+        ctx.schur_solve_multi(1, 0, 0, 33, z, z.clone())
+    with pytest.raises(gs.GschurError):   # the multi-source solve runs low-precision inner solves
+        ctx.schur_solve_multi(1, 0, 0, 1, z, z.clone(), gs.gs_default_opts(inner_prec=gs.GS_F64))
+    ctx.close()
