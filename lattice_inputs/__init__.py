@@ -356,6 +356,7 @@ def workload_gauge(name):
     * ``"16^3x32 eps0.25 ape5"``  : 16^3 x 32, exp(i 0.25 H) seed 2, 5 APE steps alpha 0.5
     * ``"24^3x48 eps0.2"``        : 24^3 x 48, exp(i 0.2 H), seed 3
     * ``"16^4 eps0.2"``           : 16^4, exp(i 0.2 H), seed 4
+    * ``"8^4 eps0.2"``            : 8^4, exp(i 0.2 H), seed 6
     * ``"32^3x64 eps0.2 ape10"``  : 32^3 x 64, exp(i 0.2 H) seed 5, 10 APE steps alpha 0.5
     """
     table = {
@@ -365,6 +366,7 @@ def workload_gauge(name):
                                  lambda d: ape_smear(random_gauge(d, 0.25, 2), d, 0.5, 5)),
         "24^3x48 eps0.2": ((24, 24, 24, 48), lambda d: random_gauge(d, 0.2, 3)),
         "16^4 eps0.2": ((16, 16, 16, 16), lambda d: random_gauge(d, 0.2, 4)),
+        "8^4 eps0.2": ((8, 8, 8, 8), lambda d: random_gauge(d, 0.2, 6)),
         "32^3x64 eps0.2 ape10": ((32, 32, 32, 64),
                                  lambda d: ape_smear(random_gauge(d, 0.2, 5), d, 0.5, 10)),
     }
