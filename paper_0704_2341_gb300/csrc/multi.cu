@@ -30,19 +30,10 @@ constexpr int kMaxRhs = 32;
 
 namespace {
 
-// thread block of the multi-source kernels: a multiple of lcm(32, N), >= 128
-int multi_block(int N) {
-    int a = 32, b = N;
-    while (b) {
-        const int t = a % b;
-        a = b;
-        b = t;
-    }
-    const int l = 32 / a * N;  // lcm(32, N)
-    int B = l;
-    while (B < 128) B += l;
-    return B;
-}
+// thread block of the persistent multi-source kernel: N sources (fastest, x)
+// by ceil(128 / N) sites (y), so every thread keeps one source
+int multi_sites_per_block(int N) { return (128 + N - 1) / N; }
+constexpr int kMultiMaxThreads = 256;
 
 struct MArgs {
     const void* in;
@@ -118,7 +109,7 @@ __device__ __forceinline__ void mstencil(const MArgs& a, int64_t k, int j, float
 }
 
 template <class S>
-__global__ void __launch_bounds__(1024) k_dslash_multi(MArgs a) {
+__global__ void __launch_bounds__(128) k_dslash_multi(MArgs a) {
     const int64_t nN = a.n * a.N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nN;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -193,14 +184,15 @@ struct PMArgs {
 // partial of (block, source j, q) goes to part[(block * N + j) * 4 + q].
 template <int NV>
 __device__ void m_put_partial(float* part, const float (&v)[NV], int N, float* buf) {
-    const int B = blockDim.x;
+    const int B = blockDim.x * blockDim.y;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;  // source = t % N
 #pragma unroll
-    for (int q = 0; q < NV; ++q) buf[q * B + threadIdx.x] = v[q];
+    for (int q = 0; q < NV; ++q) buf[q * B + t] = v[q];
     __syncthreads();
-    if ((int)threadIdx.x < N * NV) {
-        const int j = threadIdx.x % N, q = threadIdx.x / N;
+    if (t < N * NV) {
+        const int j = t % N, q = t / N;
         float s = 0.f;
-        for (int t = j; t < B; t += N) s += buf[q * B + t];
+        for (int u = j; u < B; u += N) s += buf[q * B + u];
         part[((int64_t)blockIdx.x * N + j) * 4 + q] = s;
     }
     __syncthreads();
@@ -209,8 +201,9 @@ __device__ void m_put_partial(float* part, const float (&v)[NV], int N, float* b
 // every block: per-source totals in the same order; tot[q * kMaxRhs + j]
 template <int NV>
 __device__ void m_grid_total(const float* part, int N, float* tot) {
-    if ((int)threadIdx.x < N * NV) {
-        const int j = threadIdx.x % N, q = threadIdx.x / N;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if (t < N * NV) {
+        const int j = t % N, q = t / N;
         float s = 0.f;
         for (int b = 0; b < (int)gridDim.x; ++b) s += ((const volatile float*)part)[((int64_t)b * N + j) * 4 + q];
         tot[q * kMaxRhs + j] = s;
@@ -227,7 +220,7 @@ __device__ __forceinline__ float2 fd2(float2 a, float2 b) {
 }
 
 template <class S>
-__global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
+__global__ void __launch_bounds__(kMultiMaxThreads) k_bicg_persistent_multi(PMArgs P) {
     extern __shared__ float buf[];            // [3][blockDim]
     __shared__ float tot[3 * kMaxRhs];
     __shared__ float2 alpha[kMaxRhs], omega[kMaxRhs], beta[kMaxRhs], rho[kMaxRhs];
@@ -237,9 +230,10 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
     __shared__ int n_active;
     const int N = P.D.N;
     const int64_t n = P.D.n, nN = n * N;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    const int j = (int)(threadIdx.x % N);  // this thread's source (nth % N == 0)
+    const int j = threadIdx.x;                       // this thread's source
+    const int64_t site0 = blockIdx.x * (int64_t)blockDim.y + threadIdx.y;
+    const int64_t sstride = (int64_t)gridDim.x * blockDim.y;
+    const int tflat = threadIdx.y * blockDim.x + threadIdx.x;
     const int64_t slot = (int64_t)gridDim.x * N * 4;
     float* part = P.partial;
     bool ok = true;
@@ -255,8 +249,8 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
         float v[1] = {0.f};
         const double nrm2 = P.rr64[j];
         const float scale = nrm2 > 0.0 ? (float)(1.0 / sqrt(nrm2)) : 0.f;
-        for (int64_t i = tid; i < nN; i += nth) {
-            const int64_t k = i / N;
+        for (int64_t k = site0; k < n; k += sstride) {
+            const int64_t i = k * N + j;
             float f[24], z[24];
             const double2* src = P.r64 + ((int64_t)j * n + k) * 12;
 #pragma unroll
@@ -277,8 +271,8 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
         m_put_partial<1>(part, v, N, buf);
         ok = grid_sync(P.sync);
         m_grid_total<1>(part, N, tot);
-        if ((int)threadIdx.x < N) {
-            const int q = threadIdx.x;
+        if (tflat < N) {
+            const int q = tflat;
             const float b = tot[q];
             bbs[q] = rrs[q] = b;
             rho[q] = make_float2(b, 0.f);
@@ -288,7 +282,7 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
             active[q] = (b > 0.f && isfinite(b)) ? 1 : 0;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tflat == 0) {
             int a = 0;
             for (int q = 0; q < N; ++q) a += active[q];
             n_active = a;
@@ -300,8 +294,8 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
         {
             float e[2] = {0.f, 0.f};
             if (active[j]) {
-                for (int64_t i = tid; i < nN; i += nth) {
-                    const int64_t k = i / N;
+                for (int64_t k = site0; k < n; k += sstride) {
+                    const int64_t i = k * N + j;
                     float acc[24], w[24];
                     mstencil<S, true>(A, k, j, acc);
                     Store<S>::store_spinor(P.v, nN, i, acc);
@@ -316,8 +310,8 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
             m_put_partial<2>(part + slot, e, N, buf);
             if (!(ok = grid_sync(P.sync))) break;
             m_grid_total<2>(part + slot, N, tot);
-            if ((int)threadIdx.x < N && active[threadIdx.x]) {
-                const int q = threadIdx.x;
+            if (tflat < N && active[tflat]) {
+                const int q = tflat;
                 const float2 den = make_float2(tot[q], tot[kMaxRhs + q]);
                 if (den.x == 0.f && den.y == 0.f) {
                     status[q] = GS_BREAKDOWN;
@@ -337,7 +331,8 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
             float e[1] = {0.f};
             if (active[j]) {
                 const float2 al = alpha[j];
-                for (int64_t i = tid; i < nN; i += nth) {
+                for (int64_t k = site0; k < n; k += sstride) {
+                    const int64_t i = k * N + j;
                     float fr[24], fv[24], fp[24], fx[24];
                     Store<S>::template load_spinor<true>(P.r, nN, i, fr);
                     Store<S>::template load_spinor<true>(P.v, nN, i, fv);
@@ -361,8 +356,8 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
             m_put_partial<1>(part + 2 * slot, e, N, buf);
             if (!(ok = grid_sync(P.sync))) break;
             m_grid_total<1>(part + 2 * slot, N, tot);
-            if ((int)threadIdx.x < N && active[threadIdx.x]) {
-                const int q = threadIdx.x;
+            if (tflat < N && active[tflat]) {
+                const int q = tflat;
                 if (!isfinite(tot[q])) {
                     status[q] = GS_NONFINITE;
                     active[q] = 0;
@@ -378,8 +373,8 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
         {
             float e[3] = {0.f, 0.f, 0.f};
             if (active[j] > 0) {
-                for (int64_t i = tid; i < nN; i += nth) {
-                    const int64_t k = i / N;
+                for (int64_t k = site0; k < n; k += sstride) {
+                    const int64_t i = k * N + j;
                     float acc[24], w[24];
                     mstencil<S, true>(C, k, j, acc);
                     Store<S>::store_spinor(P.t, nN, i, acc);
@@ -396,8 +391,8 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
             m_put_partial<3>(part + 3 * slot, e, N, buf);
             if (!(ok = grid_sync(P.sync))) break;
             m_grid_total<3>(part + 3 * slot, N, tot);
-            if ((int)threadIdx.x < N && active[threadIdx.x] > 0) {
-                const int q = threadIdx.x;
+            if (tflat < N && active[tflat] > 0) {
+                const int q = tflat;
                 const float tt = tot[2 * kMaxRhs + q];
                 const float inv = tt > 0.f ? 1.f / tt : 0.f;
                 omega[q] = make_float2(tot[q] * inv, tot[kMaxRhs + q] * inv);
@@ -413,7 +408,8 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
             float e[3] = {0.f, 0.f, 0.f};
             if (active[j] > 0) {
                 const float2 om = omega[j];
-                for (int64_t i = tid; i < nN; i += nth) {
+                for (int64_t k = site0; k < n; k += sstride) {
+                    const int64_t i = k * N + j;
                     float fs[24], ft[24], fh[24], fx[24];
                     Store<S>::template load_spinor<true>(P.s, nN, i, fs);
                     Store<S>::template load_spinor<true>(P.t, nN, i, ft);
@@ -440,8 +436,8 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
             m_put_partial<3>(part + 4 * slot, e, N, buf);
             if (!(ok = grid_sync(P.sync))) break;
             m_grid_total<3>(part + 4 * slot, N, tot);
-            if ((int)threadIdx.x < N && active[threadIdx.x] > 0) {
-                const int q = threadIdx.x;
+            if (tflat < N && active[tflat] > 0) {
+                const int q = tflat;
                 const float2 rho_new = make_float2(tot[q], tot[kMaxRhs + q]);
                 const float rr = tot[2 * kMaxRhs + q];
                 const float2 om = omega[q];
@@ -460,14 +456,15 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
                     rho[q] = rho_new;
                 }
             }
-            if ((int)threadIdx.x < N && active[threadIdx.x] < 0) active[threadIdx.x] = 0;
+            if (tflat < N && active[tflat] < 0) active[tflat] = 0;
             __syncthreads();
         }
         // E: p = r + beta (p - omega v)
         {
             if (active[j] > 0) {
                 const float2 be = beta[j], om = omega[j];
-                for (int64_t i = tid; i < nN; i += nth) {
+                for (int64_t k = site0; k < n; k += sstride) {
+                    const int64_t i = k * N + j;
                     float fr[24], fv[24], fp[24];
                     Store<S>::template load_spinor<true>(P.r, nN, i, fr);
                     Store<S>::template load_spinor<true>(P.v, nN, i, fv);
@@ -483,7 +480,7 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
                     Store<S>::store_spinor(P.p, nN, i, fp);
                 }
             }
-            if (threadIdx.x == 0) {
+            if (tflat == 0) {
                 int a = 0;
                 for (int q = 0; q < N; ++q) a += active[q] > 0;
                 n_active = a;
@@ -493,14 +490,14 @@ __global__ void __launch_bounds__(1024) k_bicg_persistent_multi(PMArgs P) {
         }
     }
     if (blockIdx.x == 0) {
-        if ((int)threadIdx.x < N) {
-            const int q = threadIdx.x;
+        if (tflat < N) {
+            const int q = tflat;
             P.st->iter[q] = iters[q];
             P.st->status[q] = ok ? status[q] : (int)GS_TIMEOUT;
             P.st->rr[q] = rrs[q];
             P.st->bb[q] = bbs[q];
         }
-        if (threadIdx.x == 0) {
+        if (tflat == 0) {
             P.st->lockstep_iters = it;
             P.st->err = ok ? 0 : (int)GS_TIMEOUT;
         }
@@ -670,7 +667,8 @@ static gs_status inner_solve_multi(gs_ctx* c, const Plan* p, int N, const double
     st.inner_solves += N;
     if (all) return GS_OK;
     const float lo_tol = (float)(o.lowp_tol > 0.0 ? o.lowp_tol : (prec == GS_BF16 ? 3e-2 : 1e-5));
-    const int B = multi_block(N);
+    const int SB = multi_sites_per_block(N);
+    const int B = N * SB;
     int per_sm = 0;
     const size_t dsm = 3 * (size_t)B * sizeof(float);
     auto kern = (prec == GS_BF16) ? k_bicg_persistent_multi<__nv_bfloat16>
@@ -679,7 +677,7 @@ static gs_status inner_solve_multi(gs_ctx* c, const Plan* p, int N, const double
     if (per_sm < 1) return set_err(c, GS_ECUDA, "multi-source kernel does not fit on an SM");
     int64_t g = (int64_t)per_sm * c->num_sms;
     if (c->coop_block_cap > 0 && g > c->coop_block_cap) g = c->coop_block_cap;
-    const int64_t want = (n * N + B - 1) / B;
+    const int64_t want = (n + SB - 1) / SB;
     if (g > want) g = want < c->num_sms ? (want < 1 ? 1 : want) : want;
     if (g > (int64_t)per_sm * c->num_sms) g = (int64_t)per_sm * c->num_sms;
     if (g > kMaxRedBlocks) g = kMaxRedBlocks;
@@ -737,7 +735,7 @@ static gs_status inner_solve_multi(gs_ctx* c, const Plan* p, int N, const double
         P.sync.err = (int*)(m->words + 2);
         P.st = m->st;
         void* args[] = {&P};
-        GS_CUDA(c, cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)g), dim3(B), args,
+        GS_CUDA(c, cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)g), dim3(N, SB), args,
                                                dsm, c->stream));
         c->launches++;
         GS_CUDA(c, cudaMemcpyAsync(m->st_host, m->st, sizeof(MState), cudaMemcpyDeviceToHost,
