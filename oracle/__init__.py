@@ -24,4 +24,4 @@ Parity status of each function is listed in the module headers; every
 function listed is pinned by a ``-m "not gpu"`` test except where a module
 header says "parity unpinned".
 """
-from . import dirac, permute, schur, krylov  # noqa: F401
+from . import dirac, permute, schur, krylov, net  # noqa: F401
