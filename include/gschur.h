@@ -71,6 +71,7 @@ typedef enum {
 enum { GS_TYPE_I = 1, GS_TYPE_II = 2 };
 enum { GS_F64 = 0, GS_F32 = 1, GS_BF16 = 2 };
 enum { GS_GMRES = 0, GS_BICGSTAB = 1 };
+enum { GS_INNER_BICGSTAB = 0, GS_INNER_FGMRES_NET = 1 };
 
 /* Options of schur_apply / schur_solve.  gs_default_opts fills the defaults
  * in brackets. */
@@ -92,6 +93,11 @@ typedef struct {
                             * inner_tol * ||w_b|| / ||r_j|| (at most relax_cap), accepting
                             * the solve only on a tightly recomputed true residual [1] */
     double relax_cap;      /* largest relaxed inner tolerance [1e-4] */
+    int    inner_solver;   /* low-precision stage of the mixed inner solve: GS_INNER_BICGSTAB,
+                            * or GS_INNER_FGMRES_NET = flexible GMRES(inner_restart) with the
+                            * network attached by gs_set_net as right preconditioner
+                            * [GS_INNER_BICGSTAB] */
+    int    inner_restart;  /* Krylov steps of one FGMRES-with-network pass, 1..64 [16] */
 } gs_solve_opts;
 
 /* Statistics written by schur_apply / schur_solve (may be NULL). */
@@ -295,6 +301,50 @@ gs_status gs_lowp_unpack_multi(gs_ctx* ctx, int type, int dir, int inverse, int 
                                const void* x_lp_dev, void* x_dev);
 gs_status wilson_apply_lowp_multi(gs_ctx* ctx, int type, int dir, int inverse, int prec,
                                   int nrhs, const void* x_lp_dev, void* y_lp_dev);
+
+/* z = D_rr^-1 t on the rest set of (type, dir, inverse): the inner solve of
+ * S_bb on its own (opts->inner_tol, inner_prec, inner_solver as for
+ * schur_solve).  t_dev, z_dev: complex128 [n_r][4][3] in label order (labels
+ * n_b .. V-1).  Used, for example, to make the training pairs of the learned
+ * preconditioner.  Synchronises the stream. */
+gs_status gs_solve_rr(gs_ctx* ctx, int type, int dir, int inverse, const void* t_dev, void* z_dev,
+                      const gs_solve_opts* opts, gs_solve_stats* stats);
+
+/* The learned preconditioner: a gauge-equivariant linear convolutional
+ * network M ~ D_rr^-1 with three layers, 1 -> C -> C -> 1 channels (C = 2,
+ * 4, 8 or 24).  Layer l maps activations psi(x) (channel, spin, colour) to
+ *   out(x)[R, a] = sum_{d=0..8} sum_k W_d[R, k] (U_d(x) psi(x + d))[k, a],
+ * d = 0: identity, d = 1 + mu: U_mu(x) psi(x + mu), d = 5 + mu:
+ * U_mu(x - mu)^dag psi(x - mu); R and k index (channel, spin).  The input is
+ * the rest-set vector embedded in the lattice (zero on the coarse sites); the
+ * output is read on the rest set.  The paper has no learned component; its
+ * own preconditioner is a hand-made approximation of the Schur complement
+ * (Section 3, Section 4): this one is fitted to pairs (t, D_rr^-1 t) that
+ * gs_solve_rr produces.  FP32 arithmetic; FP32 master weights for training,
+ * BF16 weights for inference.  A network is not tied to a context: it uses
+ * the links of the context it is called with. */
+typedef struct gs_net gs_net;
+gs_status gs_net_create(gs_net** net_out, int channels);
+gs_status gs_net_destroy(gs_net* net);
+/* w_host: complex64 [9][4 C_out][4 C_in] = W_d[R][k] of layer 0, 1 or 2 (host
+ * memory; resets the optimiser state). */
+gs_status gs_net_set_weights(gs_net* net, int layer, const void* w_host);
+/* what = 0: the FP32 weights, 1: the weight gradients of the last training
+ * step; same layout as gs_net_set_weights (host memory). */
+gs_status gs_net_get(gs_net* net, int what, int layer, void* host_out);
+/* y = M t on the rest set; t_dev, y_dev complex128 [n_r][4][3] (label order).
+ * Asynchronous. */
+gs_status gs_net_apply(gs_ctx* ctx, gs_net* net, int type, int dir, int inverse,
+                       const void* t_dev, void* y_dev);
+/* One training step on `batch` pairs: t_dev, z_dev complex64 [batch][n_r][4][3]
+ * with z = D_rr^-1 t.  Loss = mean over the batch of ||M t - z||^2 / ||z||^2
+ * (*loss_out); gradients by the backward kernels; with update != 0 one Adam
+ * step (lr; beta1 0.9, beta2 0.999, eps 1e-8).  Synchronises the stream. */
+gs_status gs_net_train_step(gs_ctx* ctx, gs_net* net, int type, int dir, int inverse, int batch,
+                            const void* t_dev, const void* z_dev, float lr, int update,
+                            float* loss_out);
+/* Attach (or with NULL detach) the network used by GS_INNER_FGMRES_NET. */
+gs_status gs_set_net(gs_ctx* ctx, gs_net* net);
 
 /* Text of the last error on this context ("" if none).  The pointer stays
  * valid until the next call on the context. */

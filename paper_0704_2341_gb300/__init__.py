@@ -7,7 +7,7 @@ The compute path is the CUDA library ``libgschur.so`` (C ABI in
 callers only for device memory and streams.
 """
 from ._binding import *  # noqa: F401,F403
-from ._binding import (Context, GschurError, EXPORTS, LIB_PATH, gs_default_opts,  # noqa: F401
+from ._binding import (Context, GschurError, EXPORTS, LIB_PATH, Net, gs_default_opts,  # noqa: F401
                        gs_solve_opts, gs_solve_stats, lib)
 
 __all__ = ["Context", "GschurError", "gs_create", "gs_destroy", "gs_set_gauge",
@@ -18,6 +18,7 @@ __all__ = ["Context", "GschurError", "gs_create", "gs_destroy", "gs_set_gauge",
            "gs_get_option", "GS_OPT_STENCIL_VARIANT", "GS_OPT_INNER_KERNEL", "GS_PROF_STENCIL_F64",
            "GS_PROF_STENCIL_F32", "GS_PROF_STENCIL_BF16", "GS_PROF_SOLVER_F64", "GS_PROF_SOLVER_LP",
            "schur_solve_multi", "schur_solve_batched", "gs_lowp_pack_multi", "gs_lowp_unpack_multi",
-           "wilson_apply_lowp_multi",
+           "wilson_apply_lowp_multi", "gs_solve_rr", "Net", "gs_set_net", "GS_INNER_BICGSTAB",
+           "GS_INNER_FGMRES_NET",
            "GS_TYPE_I", "GS_TYPE_II", "GS_F64", "GS_F32", "GS_BF16", "GS_GMRES",
            "GS_BICGSTAB", "GS_OK", "GS_MAXITER"]

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOMEM", 3: "GS_MAXITER",
 GS_TYPE_I, GS_TYPE_II = 1, 2
 GS_F64, GS_F32, GS_BF16 = 0, 1, 2
 GS_GMRES, GS_BICGSTAB = 0, 1
+GS_INNER_BICGSTAB, GS_INNER_FGMRES_NET = 0, 1
 GS_OPT_STENCIL_VARIANT, GS_OPT_INNER_KERNEL = 1, 2
 GS_PROF_STENCIL_F64, GS_PROF_STENCIL_F32, GS_PROF_STENCIL_BF16, GS_PROF_SOLVER_F64, \
     GS_PROF_SOLVER_LP = range(5)
@@ -31,7 +32,9 @@ EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson
            "gs_last_error", "gs_version", "gs_profile", "gs_profile_read",
            "wilson_apply_noalloc", "gs_lowp_pack", "gs_lowp_unpack", "wilson_apply_lowp", "gs_set_option",
            "gs_get_option", "schur_solve_multi", "schur_solve_batched", "gs_lowp_pack_multi",
-           "gs_lowp_unpack_multi", "wilson_apply_lowp_multi")
+           "gs_lowp_unpack_multi", "wilson_apply_lowp_multi", "gs_solve_rr", "gs_net_create",
+           "gs_net_destroy", "gs_net_set_weights", "gs_net_get", "gs_net_apply",
+           "gs_net_train_step", "gs_set_net")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -40,7 +43,8 @@ class gs_solve_opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("inner_max_iter", ctypes.c_int),
                 ("inner_prec", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("lowp_tol", ctypes.c_double), ("inner_relax", ctypes.c_int),
-                ("relax_cap", ctypes.c_double)]
+                ("relax_cap", ctypes.c_double), ("inner_solver", ctypes.c_int),
+                ("inner_restart", ctypes.c_int)]
 
 
 class gs_solve_stats(ctypes.Structure):
@@ -91,6 +95,16 @@ def _load():
         "gs_profile_read": (i32, [vp, i32, ctypes.POINTER(gs_kernel_profile)]),
         "gs_lowp_pack": (i32, [vp, i32, i32, i32, i32, vp, vp]),
         "gs_set_option": (i32, [vp, i32, i32]),
+        "gs_solve_rr": (i32, [vp, i32, i32, i32, vp, vp, ctypes.POINTER(gs_solve_opts),
+                              ctypes.POINTER(gs_solve_stats)]),
+        "gs_net_create": (i32, [ctypes.POINTER(vp), i32]),
+        "gs_net_destroy": (i32, [vp]),
+        "gs_net_set_weights": (i32, [vp, i32, vp]),
+        "gs_net_get": (i32, [vp, i32, i32, vp]),
+        "gs_net_apply": (i32, [vp, vp, i32, i32, i32, vp, vp]),
+        "gs_net_train_step": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, ctypes.c_float, i32,
+                                    ctypes.POINTER(ctypes.c_float)]),
+        "gs_set_net": (i32, [vp, vp]),
         "schur_solve_multi": (i32, [vp, i32, i32, i32, i32, vp, vp, ctypes.POINTER(gs_solve_opts),
                                     ctypes.POINTER(gs_solve_stats)]),
         "schur_solve_batched": (i32, [i32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
@@ -268,6 +282,73 @@ def wilson_apply_lowp_multi(ctx, ptype, dir, inverse, prec, nrhs, x_lp, y_lp):
                                                    _ptr(x_lp), _ptr(y_lp)))
 
 
+def gs_solve_rr(ctx, ptype, dir, inverse, t, z, opts=None, allow=(GS_OK,)):
+    o = opts if opts is not None else gs_default_opts()
+    st = gs_solve_stats()
+    _check(ctx, lib.gs_solve_rr(ctx, ptype, dir, int(bool(inverse)), _ptr(t), _ptr(z),
+                                ctypes.byref(o), ctypes.byref(st)), allow)
+    return st
+
+
+class Net:
+    """Owns one gs_net (weights as numpy complex64 [9][4 C_out][4 C_in] per layer)."""
+
+    def __init__(self, channels):
+        h = ctypes.c_void_p()
+        st = lib.gs_net_create(ctypes.byref(h), int(channels))
+        if st != GS_OK:
+            raise GschurError(st, "gs_net_create failed")
+        self.handle = h.value
+        self.channels = int(channels)
+
+    def shapes(self):
+        C = self.channels
+        return [(9, 4 * C, 4), (9, 4 * C, 4 * C), (9, 4, 4 * C)]
+
+    def set_weights(self, layer, w):
+        import numpy as np
+        a = np.ascontiguousarray(w, dtype=np.complex64)
+        if a.shape != self.shapes()[layer]:
+            raise ValueError("weights of layer %d must have shape %s" % (layer, self.shapes()[layer]))
+        st = lib.gs_net_set_weights(self.handle, layer, a.ctypes.data)
+        if st != GS_OK:
+            raise GschurError(st, "gs_net_set_weights failed")
+
+    def get(self, what, layer):
+        import numpy as np
+        a = np.empty(self.shapes()[layer], dtype=np.complex64)
+        st = lib.gs_net_get(self.handle, what, layer, a.ctypes.data)
+        if st != GS_OK:
+            raise GschurError(st, "gs_net_get failed")
+        return a
+
+    def apply(self, ctx, ptype, dir, inverse, t, y):
+        return _check(ctx, lib.gs_net_apply(ctx, self.handle, ptype, dir, int(bool(inverse)),
+                                            _ptr(t), _ptr(y)))
+
+    def train_step(self, ctx, ptype, dir, inverse, batch, t, z, lr, update=True):
+        loss = ctypes.c_float()
+        _check(ctx, lib.gs_net_train_step(ctx, self.handle, ptype, dir, int(bool(inverse)), batch,
+                                          _ptr(t), _ptr(z), float(lr), int(bool(update)),
+                                          ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if self.handle:
+            lib.gs_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gs_set_net(ctx, net):
+    return _check(ctx, lib.gs_set_net(ctx, net.handle if net is not None else None))
+
+
 def gs_set_option(ctx, option, value):
     return _check(ctx, lib.gs_set_option(ctx, option, value))
 
@@ -358,6 +439,12 @@ class Context:
 
     def profile_read(self, prec=GS_F64):
         return gs_profile_read(self.handle, prec)
+
+    def solve_rr(self, ptype, dir, inverse, t, z, opts=None, allow=(GS_OK,)):
+        return gs_solve_rr(self.handle, ptype, dir, inverse, t, z, opts, allow)
+
+    def set_net(self, net):
+        return gs_set_net(self.handle, net)
 
     def set_option(self, option, value):
         return gs_set_option(self.handle, option, value)

@@ -27,6 +27,16 @@ gs_status check_opts(gs_ctx* c, const gs_solve_opts& o) {
         return set_err(c, GS_EINVAL, "lowp_tol must be in [0, 1)");
     if (o.inner_relax && (!(o.relax_cap > 0.0) || o.relax_cap >= 1.0))
         return set_err(c, GS_EINVAL, "relax_cap must be in (0, 1)");
+    if (o.inner_solver != GS_INNER_BICGSTAB && o.inner_solver != GS_INNER_FGMRES_NET)
+        return set_err(c, GS_EINVAL, "unknown inner solver %d", o.inner_solver);
+    if (o.inner_solver == GS_INNER_FGMRES_NET) {
+        if (!c->net) return set_err(c, GS_EINVAL, "GS_INNER_FGMRES_NET needs a network (gs_set_net)");
+        if (o.inner_prec == GS_F64)
+            return set_err(c, GS_EINVAL, "GS_INNER_FGMRES_NET runs inside the mixed inner solve: "
+                                         "inner_prec must be GS_F32 or GS_BF16");
+        if (o.inner_restart < 1 || o.inner_restart > kMaxRestart)
+            return set_err(c, GS_EINVAL, "inner_restart %d not in 1..%d", o.inner_restart, kMaxRestart);
+    }
     return GS_OK;
 }
 
@@ -57,6 +67,8 @@ void gs_default_opts(gs_solve_opts* o) {
     o->lowp_tol = 0.0;
     o->inner_relax = 1;
     o->relax_cap = 1e-4;
+    o->inner_solver = GS_INNER_BICGSTAB;
+    o->inner_restart = 16;
 }
 
 const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -116,6 +128,7 @@ gs_status gs_destroy(gs_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     free_multi(c);
+    free_net_ctx(c);
     free_mixed(c);
     free_persist(c);
     for (Plan* p : c->plans) free_plan(p);
@@ -195,6 +208,7 @@ gs_status gs_set_gauge(gs_ctx* c, const void* U_dev) {
     GS_CUDA(c, cudaMemcpyAsync(c->U_abi, U_dev, (size_t)c->V * 36 * sizeof(double2),
                                cudaMemcpyDeviceToDevice, c->stream));
     c->have_gauge = true;
+    c->net_links_fresh = false;
     invalidate_mixed_links(c);
     for (Plan* p : c->plans) {
         gs_status s = pack_plan_links(c, p);
@@ -251,6 +265,31 @@ gs_status gs_get_permutation(gs_ctx* c, int type, int dir, int inverse, int32_t*
     GS_CUDA(c, cudaMemcpyAsync(perm_dev, p->perm, (size_t)c->V * sizeof(int32_t),
                                cudaMemcpyDeviceToDevice, c->stream));
     return GS_OK;
+}
+
+gs_status gs_solve_rr(gs_ctx* c, int type, int dir, int inverse, const void* t_dev, void* z_dev,
+                      const gs_solve_opts* opts, gs_solve_stats* stats) {
+    if (check_ctx(c) != GS_OK) return GS_EINVAL;
+    gs_solve_opts o;
+    gs_default_opts(&o);
+    if (opts) o = *opts;
+    gs_solve_stats st;
+    memset(&st, 0, sizeof st);
+    const long long l0 = c->launches, s0 = c->stencil_sites;
+    gs_status s = check_opts(c, o);
+    if (s == GS_OK && (!t_dev || !z_dev)) s = set_err(c, GS_EINVAL, "null vector");
+    if (s == GS_OK && type != GS_TYPE_I && type != GS_TYPE_II)
+        s = set_err(c, GS_EINVAL, "unknown permutation type %d", type);
+    if (s == GS_OK && !c->have_gauge) s = set_err(c, GS_ENOGAUGE, "no gauge field set");
+    Plan* p = nullptr;
+    if (s == GS_OK) s = get_plan(c, type, dir, inverse, &p);
+    if (s == GS_OK) {
+        s = gs::inner_solve(c, p, (const double2*)t_dev, (double2*)z_dev, o, st);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess && s == GS_OK) s = set_err(c, GS_ECUDA, "gs_solve_rr: %s", cudaGetErrorString(e));
+    }
+    finish_stats(c, stats, st, s, l0, s0);
+    return s;
 }
 
 gs_status schur_apply(gs_ctx* c, int type, int dir, int inverse, const void* xb_dev, void* yb_dev,

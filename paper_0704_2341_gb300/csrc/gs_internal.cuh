@@ -199,6 +199,16 @@ struct gs_ctx {
     void* persist = nullptr;           // persistent-solver scratch (persistent.cu)
     void* multi = nullptr;             // multi-RHS workspaces (multi.cu)
     int coop_block_cap = 0;            // cap on cooperative grids (0 = whole GPU; batched solves)
+    struct gs_net* net = nullptr;      // learned preconditioner attached with gs_set_net (net.cu)
+    bool net_links_fresh = false;      // the network's FP32 link copy matches U_abi
+    double2 *fg_V = nullptr, *fg_Z = nullptr, *fg_w = nullptr;  // FGMRES-net vectors
+    int64_t fg_cap = 0;
+    int fg_m = 0;
+    double2* fg_h = nullptr;           // device H column (2 (m+2) + 1)
+    double2* fg_h_host = nullptr;
+    double2* fg_y = nullptr;
+    double2* fg_y_host = nullptr;
+    gs::RedScratch fg_red;
     int tuned_variant = 0;             // the variant the autotuner picked last
     std::string err;
 };
@@ -300,6 +310,9 @@ struct LowpTables {
 };
 gs_status lowp_tables(gs_ctx* c, const Plan* p, int prec, LowpTables* out);
 void free_multi(gs_ctx* c);
+void free_net_ctx(gs_ctx* c);
+gs_status inner_fgmres_net(gs_ctx* c, const Plan* p, const double2* r, double2* e, double tol,
+                           int m, int* iters_out);
 void free_persist(gs_ctx* c);
 gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs& C,
                               const double2* b, double2* x, InnerWork& w, int64_t n, double tol,

@@ -650,7 +650,20 @@ gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2*
     for (; cycles < 100 && rr > target; ++cycles) {
         if (stalls >= 2) break;
         int it = 0, status = 0;
-        if (c->opt_inner_kernel == 0) {
+        if (o.inner_solver == GS_INNER_FGMRES_NET) {
+            // flexible GMRES with the network as right preconditioner; its FP64
+            // correction is added to z below in place of the low-precision one
+            if (m->e64_cap < n) {
+                cudaFree(m->e64);
+                m->e64 = nullptr;
+                if (cudaMalloc(&m->e64, (size_t)n * kSiteC * sizeof(double2)) != cudaSuccess) {
+                    cudaGetLastError();
+                    return set_err(c, GS_ENOMEM, "allocating the FP64 correction failed");
+                }
+                m->e64_cap = n;
+            }
+            s = inner_fgmres_net(c, p, r64, m->e64, lo_tol, o.inner_restart, &it);
+        } else if (c->opt_inner_kernel == 0) {
             // init + all iterations of the cycle in one cooperative launch
             LpArgs A;
             memset(&A, 0, sizeof A);
@@ -711,12 +724,18 @@ gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2*
         if (s != GS_OK) return s;
         iters_total += it;
         // z += ||r|| e ; r = t - D_rr z (FP64) ; ||r||^2
-        if (prec == GS_BF16)
-            k_lp_accum<__nv_bfloat16><<<gp, kLpRed, 0, c->stream>>>(w.x, w.rr64, z, n);
-        else
-            k_lp_accum<float><<<gp, kLpRed, 0, c->stream>>>(w.x, w.rr64, z, n);
-        c->launches++;
-        GS_CHECK_LAUNCH(c);
+        if (o.inner_solver == GS_INNER_FGMRES_NET) {
+            if ((s = launch_axpby(c, make_double2(1.0, 0.0), m->e64, make_double2(1.0, 0.0), z,
+                                  n * kSiteC)) != GS_OK)
+                return s;
+        } else {
+            if (prec == GS_BF16)
+                k_lp_accum<__nv_bfloat16><<<gp, kLpRed, 0, c->stream>>>(w.x, w.rr64, z, n);
+            else
+                k_lp_accum<float><<<gp, kLpRed, 0, c->stream>>>(w.x, w.rr64, z, n);
+            c->launches++;
+            GS_CHECK_LAUNCH(c);
+        }
         if ((s = launch_stencil_f64(c, ra)) != GS_OK) return s;
         if ((s = launch_norm2(c, red, r64, n * kSiteC, w.rr64)) != GS_OK) return s;
         GS_CUDA(c, cudaMemcpyAsync(w.rr64_host, w.rr64, sizeof(double), cudaMemcpyDeviceToHost,

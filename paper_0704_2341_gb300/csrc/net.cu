@@ -1,0 +1,842 @@
+// Gauge-equivariant linear convolutional network: the learned preconditioner
+// M ~ D_rr^-1 of the inner solve (forward, backward, Adam training step,
+// inference) and flexible GMRES with M as right preconditioner.
+//
+// Layer (C_in -> C_out channels, activations [site][channel][spin][colour]):
+//   out(x)[R, a] = sum_{d=0..8} sum_k W_d[R, k] (U_d(x) in(x + d))[k, a]
+// with k = (channel, spin) of the input, R = (channel, spin) of the output and
+// the nine parallel transports d = 0 (identity), 1 + mu (U_mu(x) in(x+mu)),
+// 5 + mu (U_mu(x-mu)^dag in(x-mu)).  The network is 1 -> C -> C -> 1; its
+// input is the rest-set vector embedded in the lattice (zero on the coarse
+// sites), its output is read on the rest set.
+//
+// GB300 mapping: a block computes one tile of 8 sites x 3 colours (24 GEMM
+// columns) for all output rows: the transported neighbour activations of the
+// tile go to shared memory, each thread owns one output row and streams the
+// weight column W_d[R, :] (stored transposed, [d][k][R], so a warp reads
+// consecutive rows), accumulating 24 complex outputs in FP32 registers.
+// Weights are kept in FP32 (training master) and BF16 (inference).
+// Backward: the input gradient is the same convolution with W'_d =
+// (W_{reverse(d)})^H; the weight gradient g_W_d = sum_{x,a} g_out(x) T_d(x)^H
+// is accumulated per (site chunk, d) block and reduced over chunks in a fixed
+// order (deterministic).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <complex>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+struct gs_net {
+    int C = 0;
+    float2* W[3] = {};       // FP32 master, transposed [9][K][R]
+    __nv_bfloat162* Wb[3] = {};  // BF16 copy
+    float2* G[3] = {};       // gradients (same layout)
+    float2* Wp = nullptr;    // transformed weights of the backward input conv (max size)
+    float* m[3] = {};        // Adam moments (as floats)
+    float* v[3] = {};
+    int64_t nel[3] = {};     // complex entries per layer
+    long long step = 0;
+    // scratch sized for a lattice
+    int64_t capV = 0;
+    float2* act[4] = {};     // act0 [V][4][3], act1/2 [V][4C][3], act3 [V][4][3]
+    float2* gact[2] = {};    // gradient buffers [V][4C][3]
+    float2* partial = nullptr;  // [chunks][9][K][R]
+    float2* U32 = nullptr;      // FP32 links [V][4][9] (site order) of the last context
+    const void* U32_src = nullptr;
+    float* red = nullptr;       // small reduction scratch
+    unsigned int* counter = nullptr;
+    float* host_red = nullptr;
+};
+
+namespace gs {
+namespace {
+
+constexpr int kTS = 8;           // sites per tile
+constexpr int kNCol = kTS * 3;   // GEMM columns per tile
+constexpr int kChunks = 32;      // site chunks of the weight gradient
+
+__device__ __forceinline__ float2 cm(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void cfma2(float2& acc, float2 a, float2 b) {  // acc += a b
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfmaconj(float2& acc, float2 a, float2 b) {  // acc += a conj(b)
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(a.y, b.x, acc.y);
+    acc.y = fmaf(-a.x, b.y, acc.y);
+}
+
+__device__ __forceinline__ float2 loadw(const float2* W, int64_t i) { return __ldg(W + i); }
+__device__ __forceinline__ float2 loadw(const __nv_bfloat162* W, int64_t i) {
+    return __bfloat1622float2(W[i]);
+}
+
+// transported activations of one tile for transport d:
+// T[k][s*3 + a] = (U_d(x_s) in(x_s + d))[k, a]; threads stride over (s, k)
+template <int K>
+__device__ __forceinline__ void stage_tile(const float2* __restrict__ in, const float2* __restrict__ U32,
+                                           const int2* __restrict__ nbr, int64_t base, int64_t V, int d,
+                                           float2 (*T)[kNCol]) {
+    for (int e = threadIdx.x; e < kTS * K; e += blockDim.x) {
+        const int s = e / K, k = e - s * K;
+        const int64_t x = base + s;
+        float2 t0 = make_float2(0.f, 0.f), t1 = t0, t2 = t0;
+        if (x < V) {
+            int64_t y = x;
+            const float2* u = nullptr;
+            bool dag = false;
+            if (d >= 1 && d <= 4) {
+                const int mu = d - 1;
+                y = __ldg(nbr + x * 4 + mu).x;
+                u = U32 + (x * 4 + mu) * 9;
+            } else if (d >= 5) {
+                const int mu = d - 5;
+                y = __ldg(nbr + x * 4 + mu).y;
+                u = U32 + (y * 4 + mu) * 9;
+                dag = true;
+            }
+            const float2* src = in + (y * K + k) * 3;
+            const float2 p0 = src[0], p1 = src[1], p2 = src[2];
+            if (!u) {
+                t0 = p0;
+                t1 = p1;
+                t2 = p2;
+            } else if (!dag) {
+                float2 r[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cfma2(r[a], __ldg(u + 3 * a + 0), p0);
+                    cfma2(r[a], __ldg(u + 3 * a + 1), p1);
+                    cfma2(r[a], __ldg(u + 3 * a + 2), p2);
+                }
+                t0 = r[0];
+                t1 = r[1];
+                t2 = r[2];
+            } else {  // U^dag: row a = conj of column a
+                float2 r[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float2 c0 = __ldg(u + 0 + a), c1 = __ldg(u + 3 + a), c2 = __ldg(u + 6 + a);
+                    cfma2(r[a], make_float2(c0.x, -c0.y), p0);
+                    cfma2(r[a], make_float2(c1.x, -c1.y), p1);
+                    cfma2(r[a], make_float2(c2.x, -c2.y), p2);
+                }
+                t0 = r[0];
+                t1 = r[1];
+                t2 = r[2];
+            }
+        }
+        T[k][s * 3 + 0] = t0;
+        T[k][s * 3 + 1] = t1;
+        T[k][s * 3 + 2] = t2;
+    }
+}
+
+// out[V][R4][3] = sum_d W_d T_d ; threads: one per output row (>= 32)
+template <int CIN, int COUT, class WT>
+__global__ void k_net_conv(const float2* __restrict__ in, float2* __restrict__ out, const WT* __restrict__ W,
+                           const float2* __restrict__ U32, const int2* __restrict__ nbr, int64_t V) {
+    constexpr int K = 4 * CIN, R4 = 4 * COUT;
+    __shared__ float2 T[K][kNCol];
+    const int R = threadIdx.x;
+    for (int64_t base = (int64_t)blockIdx.x * kTS; base < V; base += (int64_t)gridDim.x * kTS) {
+        float2 acc[kNCol];
+#pragma unroll
+        for (int q = 0; q < kNCol; ++q) acc[q] = make_float2(0.f, 0.f);
+        for (int d = 0; d < 9; ++d) {
+            stage_tile<K>(in, U32, nbr, base, V, d, T);
+            __syncthreads();
+            if (R < R4) {
+                const WT* wd = W + (int64_t)d * K * R4 + R;
+                for (int k = 0; k < K; ++k) {
+                    const float2 w = loadw(wd, (int64_t)k * R4);
+#pragma unroll
+                    for (int q = 0; q < kNCol; ++q) cfma2(acc[q], w, T[k][q]);
+                }
+            }
+            __syncthreads();
+        }
+        if (R < R4) {
+#pragma unroll
+            for (int s = 0; s < kTS; ++s) {
+                const int64_t x = base + s;
+                if (x < V) {
+                    float2* dst = out + (x * R4 + R) * 3;
+                    dst[0] = acc[s * 3 + 0];
+                    dst[1] = acc[s * 3 + 1];
+                    dst[2] = acc[s * 3 + 2];
+                }
+            }
+        }
+    }
+}
+
+// partial[chunk][d][k][R] = sum over the chunk's sites and colours of
+// g_out(x)[R, a] conj(T_d(x)[k, a]);  grid = (kChunks, 9)
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_net_gradw(const float2* __restrict__ in, const float2* __restrict__ gout,
+                                                  float2* __restrict__ partial, const float2* __restrict__ U32,
+                                                  const int2* __restrict__ nbr, int64_t V) {
+    constexpr int K = 4 * CIN, R4 = 4 * COUT, NE = K * R4;
+    constexpr int PER = (NE + 255) / 256;
+    __shared__ float2 T[K][kNCol];
+    __shared__ float2 Gs[R4][kNCol];
+    const int chunk = blockIdx.x, d = blockIdx.y;
+    const int64_t tiles = (V + kTS - 1) / kTS;
+    const int64_t t0 = tiles * chunk / gridDim.x, t1 = tiles * (chunk + 1) / gridDim.x;
+    float2 acc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        const int64_t base = tile * kTS;
+        stage_tile<K>(in, U32, nbr, base, V, d, T);
+        for (int e = threadIdx.x; e < R4 * kNCol; e += blockDim.x) {
+            const int R = e / kNCol, col = e - R * kNCol;
+            const int s = col / 3, a = col - s * 3;
+            const int64_t x = base + s;
+            Gs[R][col] = (x < V) ? gout[(x * R4 + R) * 3 + a] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = threadIdx.x + q * 256;
+            if (e < NE) {
+                const int k = e / R4, R = e - k * R4;
+                float2 s = acc[q];
+#pragma unroll 8
+                for (int col = 0; col < kNCol; ++col) cfmaconj(s, Gs[R][col], T[k][col]);
+                acc[q] = s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int e = threadIdx.x + q * 256;
+        if (e < NE) partial[((int64_t)chunk * 9 + d) * NE + e] = acc[q];
+    }
+}
+
+// G (+)= sum over chunks of the partials (fixed order)
+__global__ void k_net_reduce(const float2* __restrict__ partial, float2* __restrict__ G, int64_t nel,
+                             int chunks, int accumulate) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nel;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float2 s = accumulate ? G[i] : make_float2(0.f, 0.f);
+        for (int c = 0; c < chunks; ++c) {
+            const float2 p = partial[(int64_t)c * nel + i];
+            s.x += p.x;
+            s.y += p.y;
+        }
+        G[i] = s;
+    }
+}
+
+// W' of the backward input convolution: W'T[d'][R][k] = conj(WT[d][k][R]),
+// d' the reversed transport (0 -> 0, +mu <-> -mu)
+__global__ void k_net_wprime(const float2* __restrict__ W, float2* __restrict__ Wp, int K, int R4) {
+    const int64_t n = 9LL * K * R4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(i / ((int64_t)K * R4));
+        const int64_t rem = i - (int64_t)d * K * R4;
+        const int k = (int)(rem / R4), R = (int)(rem - (int64_t)k * R4);
+        const int dp = d == 0 ? 0 : (d <= 4 ? d + 4 : d - 4);
+        const float2 w = W[i];
+        Wp[((int64_t)dp * R4 + R) * K + k] = make_float2(w.x, -w.y);
+    }
+}
+
+// rest vector (label order, complex128 or complex64) -> whole lattice (site order), zero on b
+__global__ void k_net_embed64(const double2* __restrict__ t, const int32_t* __restrict__ perm, int64_t nb,
+                              int64_t nr, float2* __restrict__ full) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr * 12;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / 12;
+        const int c = (int)(i - k * 12);
+        const double2 v = t[i];
+        full[(int64_t)perm[nb + k] * 12 + c] = make_float2((float)v.x, (float)v.y);
+    }
+}
+__global__ void k_net_embed32(const float2* __restrict__ t, const int32_t* __restrict__ perm, int64_t nb,
+                              int64_t nr, float2* __restrict__ full) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr * 12;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / 12;
+        const int c = (int)(i - k * 12);
+        full[(int64_t)perm[nb + k] * 12 + c] = t[i];
+    }
+}
+__global__ void k_net_restrict64(const float2* __restrict__ full, const int32_t* __restrict__ perm,
+                                 int64_t nb, int64_t nr, double2* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr * 12;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / 12;
+        const int c = (int)(i - k * 12);
+        const float2 v = full[(int64_t)perm[nb + k] * 12 + c];
+        y[i] = make_double2((double)v.x, (double)v.y);
+    }
+}
+
+// loss of one sample: sums ||y_r - z||^2 and ||z||^2 into red[0..1]
+// (last-block pattern), then g_y = coef (y - z) on r, 0 on b
+__global__ void k_net_loss(const float2* __restrict__ yfull, const float2* __restrict__ z,
+                           const int32_t* __restrict__ perm, int64_t nb, int64_t nr, float* red,
+                           unsigned int* counter) {
+    __shared__ float sm[2][32];
+    __shared__ bool last;
+    float a = 0.f, b = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr * 12;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / 12;
+        const int c = (int)(i - k * 12);
+        const float2 y = yfull[(int64_t)perm[nb + k] * 12 + c], zz = z[i];
+        const float dx = y.x - zz.x, dy = y.y - zz.y;
+        a = fmaf(dx, dx, fmaf(dy, dy, a));
+        b = fmaf(zz.x, zz.x, fmaf(zz.y, zz.y, b));
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        sm[0][warp] = a;
+        sm[1][warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s0 = 0.f, s1 = 0.f;
+        for (int w = 0; w < nw; ++w) {
+            s0 += sm[0][w];
+            s1 += sm[1][w];
+        }
+        red[2 + 2 * blockIdx.x] = s0;
+        red[3 + 2 * blockIdx.x] = s1;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        float s0 = 0.f, s1 = 0.f;
+        for (unsigned bl = 0; bl < gridDim.x; ++bl) {
+            s0 += ((volatile float*)red)[2 + 2 * bl];
+            s1 += ((volatile float*)red)[3 + 2 * bl];
+        }
+        red[0] = s0;
+        red[1] = s1;
+        *counter = 0u;
+    }
+}
+
+__global__ void k_net_lossgrad(const float2* __restrict__ yfull, const float2* __restrict__ z,
+                               const int32_t* __restrict__ perm, int64_t nb, int64_t nr,
+                               const float* __restrict__ red, float scale, float2* __restrict__ gfull) {
+    const float coef = 2.f * scale / red[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr * 12;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / 12;
+        const int c = (int)(i - k * 12);
+        const int64_t f = (int64_t)perm[nb + k] * 12 + c;
+        const float2 y = yfull[f], zz = z[i];
+        gfull[f] = make_float2(coef * (y.x - zz.x), coef * (y.y - zz.y));
+    }
+}
+
+// Adam on the real and imaginary parts; refreshes the BF16 copy
+__global__ void k_net_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                           float* __restrict__ v, __nv_bfloat16* __restrict__ wb, int64_t n, float lr,
+                           float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
+        const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+        wb[i] = __float2bfloat16_rn(wi);
+    }
+}
+
+__global__ void k_net_tobf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+__global__ void k_links32(const double2* __restrict__ U, float2* __restrict__ U32, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        U32[i] = make_float2((float)U[i].x, (float)U[i].y);
+}
+
+// layer shapes: 0: 1 -> C, 1: C -> C, 2: C -> 1
+inline void layer_dims(int C, int l, int* cin, int* cout) {
+    *cin = (l == 0) ? 1 : C;
+    *cout = (l == 2) ? 1 : C;
+}
+
+template <int C, class WT>
+void conv_dispatch_t(int cin, int cout, const float2* in, float2* out, const WT* W, const float2* U32,
+                     const int2* nbr, int64_t V, int blocks, cudaStream_t s) {
+    if (cin == 1 && cout == C) k_net_conv<1, C, WT><<<blocks, 4 * C < 32 ? 32 : 4 * C, 0, s>>>(in, out, W, U32, nbr, V);
+    else if (cin == C && cout == C) k_net_conv<C, C, WT><<<blocks, 4 * C < 32 ? 32 : 4 * C, 0, s>>>(in, out, W, U32, nbr, V);
+    else if (cin == C && cout == 1) k_net_conv<C, 1, WT><<<blocks, 32, 0, s>>>(in, out, W, U32, nbr, V);
+    else if (cin == 1 && cout == 1) k_net_conv<1, 1, WT><<<blocks, 32, 0, s>>>(in, out, W, U32, nbr, V);
+}
+
+template <int C>
+void gradw_dispatch_t(int cin, int cout, const float2* in, const float2* gout, float2* partial,
+                      const float2* U32, const int2* nbr, int64_t V, cudaStream_t s) {
+    dim3 g(kChunks, 9);
+    if (cin == 1 && cout == C) k_net_gradw<1, C><<<g, 256, 0, s>>>(in, gout, partial, U32, nbr, V);
+    else if (cin == C && cout == C) k_net_gradw<C, C><<<g, 256, 0, s>>>(in, gout, partial, U32, nbr, V);
+    else if (cin == C && cout == 1) k_net_gradw<C, 1><<<g, 256, 0, s>>>(in, gout, partial, U32, nbr, V);
+}
+
+}  // namespace
+
+static bool net_channels_ok(int C) { return C == 2 || C == 4 || C == 8 || C == 24; }
+
+template <class WT>
+static void conv_dispatch(int C, int cin, int cout, const float2* in, float2* out, const WT* W,
+                          const float2* U32, const int2* nbr, int64_t V, int blocks, cudaStream_t s) {
+    switch (C) {
+        case 2: conv_dispatch_t<2, WT>(cin, cout, in, out, W, U32, nbr, V, blocks, s); break;
+        case 4: conv_dispatch_t<4, WT>(cin, cout, in, out, W, U32, nbr, V, blocks, s); break;
+        case 8: conv_dispatch_t<8, WT>(cin, cout, in, out, W, U32, nbr, V, blocks, s); break;
+        default: conv_dispatch_t<24, WT>(cin, cout, in, out, W, U32, nbr, V, blocks, s); break;
+    }
+}
+
+static void gradw_dispatch(int C, int cin, int cout, const float2* in, const float2* gout,
+                           float2* partial, const float2* U32, const int2* nbr, int64_t V,
+                           cudaStream_t s) {
+    switch (C) {
+        case 2: gradw_dispatch_t<2>(cin, cout, in, gout, partial, U32, nbr, V, s); break;
+        case 4: gradw_dispatch_t<4>(cin, cout, in, gout, partial, U32, nbr, V, s); break;
+        case 8: gradw_dispatch_t<8>(cin, cout, in, gout, partial, U32, nbr, V, s); break;
+        default: gradw_dispatch_t<24>(cin, cout, in, gout, partial, U32, nbr, V, s); break;
+    }
+}
+
+// scratch of a network for a lattice of V sites; FP32 links of the context
+static gs_status net_prepare(gs_ctx* c, gs_net* nt) {
+    const int64_t V = c->V;
+    if (nt->capV < V) {
+        for (auto& a : nt->act) cudaFree(a);
+        for (auto& a : nt->gact) cudaFree(a);
+        cudaFree(nt->U32);
+        nt->U32 = nullptr;
+        nt->U32_src = nullptr;
+        const size_t big = (size_t)V * 4 * nt->C * 3 * sizeof(float2);
+        const size_t sm = (size_t)V * 12 * sizeof(float2);
+        if (cudaMalloc(&nt->act[0], sm) != cudaSuccess || cudaMalloc(&nt->act[1], big) != cudaSuccess ||
+            cudaMalloc(&nt->act[2], big) != cudaSuccess || cudaMalloc(&nt->act[3], sm) != cudaSuccess ||
+            cudaMalloc(&nt->gact[0], big) != cudaSuccess || cudaMalloc(&nt->gact[1], big) != cudaSuccess ||
+            cudaMalloc(&nt->U32, (size_t)V * 36 * sizeof(float2)) != cudaSuccess) {
+            cudaGetLastError();
+            nt->capV = 0;
+            return set_err(c, GS_ENOMEM, "allocating network activations failed");
+        }
+        nt->capV = V;
+    }
+    if (nt->U32_src != (const void*)c || !c->net_links_fresh) {
+        k_links32<<<grid_for(V * 36, 256, c->num_sms * 8), 256, 0, c->stream>>>(c->U_abi, nt->U32, V * 36);
+        c->launches++;
+        GS_CHECK_LAUNCH(c);
+        nt->U32_src = c;
+        c->net_links_fresh = true;
+    }
+    return GS_OK;
+}
+
+// y_full = M(x_full) with BF16 (infer) or FP32 weights; acts kept in nt->act
+static gs_status net_forward(gs_ctx* c, gs_net* nt, bool bf16) {
+    const Plan* id = c->plans[0];
+    const int64_t V = c->V;
+    const int blocks = (int)((V + kTS - 1) / kTS);
+    for (int l = 0; l < 3; ++l) {
+        int cin, cout;
+        layer_dims(nt->C, l, &cin, &cout);
+        if (bf16)
+            conv_dispatch<__nv_bfloat162>(nt->C, cin, cout, nt->act[l], nt->act[l + 1], nt->Wb[l],
+                                          nt->U32, id->nbr, V, blocks, c->stream);
+        else
+            conv_dispatch<float2>(nt->C, cin, cout, nt->act[l], nt->act[l + 1], nt->W[l], nt->U32,
+                                  id->nbr, V, blocks, c->stream);
+        c->launches++;
+        GS_CHECK_LAUNCH(c);
+    }
+    return GS_OK;
+}
+
+// y = M(t) for a rest vector (FP64 in and out), BF16 weights
+gs_status net_apply_rest(gs_ctx* c, gs_net* nt, const Plan* p, const double2* t, double2* y) {
+    gs_status s = net_prepare(c, nt);
+    if (s != GS_OK) return s;
+    const int64_t V = c->V, nb = p->nb, nr = V - nb;
+    GS_CUDA(c, cudaMemsetAsync(nt->act[0], 0, (size_t)V * 12 * sizeof(float2), c->stream));
+    const int g = grid_for(nr * 12, 256, c->num_sms * 8);
+    k_net_embed64<<<g, 256, 0, c->stream>>>(t, p->perm, nb, nr, nt->act[0]);
+    c->launches++;
+    if ((s = net_forward(c, nt, true)) != GS_OK) return s;
+    k_net_restrict64<<<g, 256, 0, c->stream>>>(nt->act[3], p->perm, nb, nr, y);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+// Flexible GMRES(m) for D_rr e = r (FP64 vectors) with the network as right
+// preconditioner: z_j = M(v_j), w = D_rr z_j, CGS2, Givens on the host;
+// e = sum_j z_j y_j.  Stops at ||r - D_rr e|| <= tol ||r|| (estimate).
+gs_status inner_fgmres_net(gs_ctx* c, const Plan* p, const double2* r, double2* e, double tol,
+                           int m, int* iters_out) {
+    gs_net* nt = c->net;
+    if (!nt) return set_err(c, GS_EINVAL, "no network attached (gs_set_net)");
+    const int64_t nb = p->nb, nr = c->V - nb, n = nr * kSiteC;
+    const size_t vb = (size_t)n * sizeof(double2);
+    if (m < 1) m = 1;
+    if (m > kMaxRestart) m = kMaxRestart;
+    if (c->fg_cap < nr || c->fg_m < m) {
+        cudaFree(c->fg_V);
+        cudaFree(c->fg_Z);
+        cudaFree(c->fg_w);
+        c->fg_V = c->fg_Z = c->fg_w = nullptr;
+        if (cudaMalloc(&c->fg_V, vb * (m + 1)) != cudaSuccess || cudaMalloc(&c->fg_Z, vb * m) != cudaSuccess ||
+            cudaMalloc(&c->fg_w, vb) != cudaSuccess) {
+            cudaGetLastError();
+            c->fg_cap = 0;
+            return set_err(c, GS_ENOMEM, "allocating FGMRES vectors failed");
+        }
+        c->fg_cap = nr;
+        c->fg_m = m;
+    }
+    if (!c->fg_h) {
+        const size_t hb = (2 * (kMaxRestart + 2) + 1) * sizeof(double2);
+        if (cudaMalloc(&c->fg_h, hb) != cudaSuccess || cudaHostAlloc(&c->fg_h_host, hb, 0) != cudaSuccess ||
+            cudaMalloc(&c->fg_y, (kMaxRestart + 1) * sizeof(double2)) != cudaSuccess ||
+            cudaHostAlloc(&c->fg_y_host, (kMaxRestart + 1) * sizeof(double2), 0) != cudaSuccess ||
+            cudaMalloc(&c->fg_red.partial, kRedScratchDoubles * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&c->fg_red.counter, sizeof(unsigned int)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, GS_ENOMEM, "allocating FGMRES scratch failed");
+        }
+        GS_CUDA(c, cudaMemsetAsync(c->fg_red.counter, 0, sizeof(unsigned int), c->stream));
+    }
+    gs_status s;
+    struct {
+        double2* hbuf;
+        double2* hbuf_host;
+        double2* y;
+        double2* y_host;
+        RedScratch red;
+    } W = {c->fg_h, c->fg_h_host, c->fg_y, c->fg_y_host, c->fg_red};
+    double2 *V = c->fg_V, *Z = c->fg_Z, *w = c->fg_w;
+    // beta = ||r||, v0 = r / beta
+    if ((s = launch_norm2(c, W.red, r, n, c->scal_dev)) != GS_OK) return s;
+    GS_CUDA(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double beta = sqrt(c->scal_host[0]);
+    GS_CUDA(c, cudaMemsetAsync(e, 0, vb, c->stream));
+    *iters_out = 0;
+    if (!(beta > 0.0)) return isfinite(beta) ? GS_OK : set_err(c, GS_NONFINITE, "non-finite FGMRES rhs");
+    if ((s = launch_scale_copy(c, r, V, n, 1.0 / beta)) != GS_OK) return s;
+    using cplx = std::complex<double>;
+    std::vector<cplx> H((size_t)(m + 1) * m), g(m + 1, 0.0), cs(m), sn(m);
+    g[0] = beta;
+    StencilArgs a;
+    memset(&a, 0, sizeof a);
+    a.o0 = nb;
+    a.n_out = nr;
+    a.a0 = nb;
+    a.a1 = c->V;
+    a.b1 = c->V;
+    a.diag = c->m0 + 4.0;
+    a.plan = p;
+    a.nbr = p->nbr;
+    a.links = p->links;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+        double2* Vj = V + (size_t)j * n;
+        double2* Zj = Z + (size_t)j * n;
+        if ((s = net_apply_rest(c, nt, p, Vj, Zj)) != GS_OK) return s;
+        a.out = w;
+        a.inA = Zj;
+        if ((s = launch_stencil_f64(c, a)) != GS_OK) return s;
+        double2* h = W.hbuf;
+        double2* h2 = W.hbuf + (m + 2);
+        if ((s = launch_multidot(c, W.red, V, n, j + 1, w, n, h, 0)) != GS_OK) return s;
+        if ((s = launch_multiaxpy(c, V, n, j + 1, h, w, n, -1)) != GS_OK) return s;
+        if ((s = launch_multidot(c, W.red, V, n, j + 1, w, n, h2, 0)) != GS_OK) return s;
+        if ((s = launch_multiaxpy(c, V, n, j + 1, h2, w, n, -1)) != GS_OK) return s;
+        if ((s = launch_norm2(c, W.red, w, n, (double*)(W.hbuf + 2 * (m + 2)))) != GS_OK) return s;
+        GS_CUDA(c, cudaMemcpyAsync(W.hbuf_host, W.hbuf, (2 * (m + 2) + 1) * sizeof(double2),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        const double hn = sqrt(W.hbuf_host[2 * (m + 2)].x);
+        if (!isfinite(hn)) return set_err(c, GS_NONFINITE, "non-finite FGMRES norm");
+        for (int i = 0; i <= j; ++i)
+            H[(size_t)i * m + j] = cplx(W.hbuf_host[i].x + W.hbuf_host[m + 2 + i].x,
+                                        W.hbuf_host[i].y + W.hbuf_host[m + 2 + i].y);
+        H[(size_t)(j + 1) * m + j] = hn;
+        if (hn > 0.0)
+            if ((s = launch_scale_copy(c, w, V + (size_t)(j + 1) * n, n, 1.0 / hn)) != GS_OK) return s;
+        for (int i = 0; i < j; ++i) {
+            const cplx h0 = H[(size_t)i * m + j], h1 = H[(size_t)(i + 1) * m + j];
+            H[(size_t)i * m + j] = std::conj(cs[i]) * h0 + std::conj(sn[i]) * h1;
+            H[(size_t)(i + 1) * m + j] = -sn[i] * h0 + cs[i] * h1;
+        }
+        const cplx aa = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+        const double hh = sqrt(std::norm(aa) + std::norm(bb));
+        cs[j] = hh > 0.0 ? aa / hh : cplx(1.0);
+        sn[j] = hh > 0.0 ? bb / hh : cplx(0.0);
+        H[(size_t)j * m + j] = hh;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = std::conj(cs[j]) * g[j];
+        k = j + 1;
+        if (std::abs(g[j + 1]) <= tol * beta || hn == 0.0) break;
+    }
+    std::vector<cplx> y(k);
+    for (int i = k - 1; i >= 0; --i) {
+        cplx acc = g[i];
+        for (int l = i + 1; l < k; ++l) acc -= H[(size_t)i * m + l] * y[l];
+        y[i] = acc / H[(size_t)i * m + i];
+    }
+    for (int i = 0; i < k; ++i) W.y_host[i] = make_double2(y[i].real(), y[i].imag());
+    GS_CUDA(c, cudaMemcpyAsync(W.y, W.y_host, k * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    if ((s = launch_multiaxpy(c, Z, n, k, W.y, e, n, +1)) != GS_OK) return s;
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    *iters_out = k;
+    return GS_OK;
+}
+
+void free_net_ctx(gs_ctx* c) {
+    cudaFree(c->fg_V);
+    cudaFree(c->fg_Z);
+    cudaFree(c->fg_w);
+    cudaFree(c->fg_h);
+    cudaFree(c->fg_y);
+    cudaFree(c->fg_red.partial);
+    cudaFree(c->fg_red.counter);
+    if (c->fg_h_host) cudaFreeHost(c->fg_h_host);
+    if (c->fg_y_host) cudaFreeHost(c->fg_y_host);
+    c->fg_V = c->fg_Z = c->fg_w = c->fg_h = c->fg_y = nullptr;
+    c->fg_h_host = c->fg_y_host = nullptr;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+gs_status gs_net_create(gs_net** out, int channels) {
+    if (!out || !net_channels_ok(channels)) return GS_EINVAL;
+    gs_net* nt = new gs_net();
+    nt->C = channels;
+    bool ok = true;
+    for (int l = 0; l < 3; ++l) {
+        int cin, cout;
+        layer_dims(channels, l, &cin, &cout);
+        nt->nel[l] = 9LL * 4 * cin * 4 * cout;
+        const size_t b = (size_t)nt->nel[l] * sizeof(float2);
+        ok = ok && cudaMalloc(&nt->W[l], b) == cudaSuccess && cudaMalloc(&nt->G[l], b) == cudaSuccess &&
+             cudaMalloc(&nt->Wb[l], (size_t)nt->nel[l] * sizeof(__nv_bfloat162)) == cudaSuccess &&
+             cudaMalloc(&nt->m[l], b) == cudaSuccess && cudaMalloc(&nt->v[l], b) == cudaSuccess;
+        if (ok) {
+            cudaMemset(nt->W[l], 0, b);
+            cudaMemset(nt->m[l], 0, b);
+            cudaMemset(nt->v[l], 0, b);
+            cudaMemset(nt->Wb[l], 0, (size_t)nt->nel[l] * sizeof(__nv_bfloat162));
+        }
+    }
+    const int64_t big = 9LL * 4 * channels * 4 * channels;
+    ok = ok && cudaMalloc(&nt->Wp, big * sizeof(float2)) == cudaSuccess &&
+         cudaMalloc(&nt->partial, (size_t)kChunks * big * sizeof(float2)) == cudaSuccess &&
+         cudaMalloc(&nt->red, 4096 * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&nt->counter, sizeof(unsigned int)) == cudaSuccess &&
+         cudaHostAlloc(&nt->host_red, 4 * sizeof(float), 0) == cudaSuccess;
+    if (ok) ok = cudaMemset(nt->counter, 0, sizeof(unsigned int)) == cudaSuccess &&
+                 cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        gs_net_destroy(nt);
+        return GS_ENOMEM;
+    }
+    *out = nt;
+    return GS_OK;
+}
+
+gs_status gs_net_destroy(gs_net* nt) {
+    if (!nt) return GS_OK;
+    cudaDeviceSynchronize();
+    for (int l = 0; l < 3; ++l) {
+        cudaFree(nt->W[l]);
+        cudaFree(nt->Wb[l]);
+        cudaFree(nt->G[l]);
+        cudaFree(nt->m[l]);
+        cudaFree(nt->v[l]);
+    }
+    for (auto& a : nt->act) cudaFree(a);
+    for (auto& a : nt->gact) cudaFree(a);
+    cudaFree(nt->Wp);
+    cudaFree(nt->partial);
+    cudaFree(nt->U32);
+    cudaFree(nt->red);
+    cudaFree(nt->counter);
+    if (nt->host_red) cudaFreeHost(nt->host_red);
+    cudaGetLastError();
+    delete nt;
+    return GS_OK;
+}
+
+// w_host: complex64 [9][4 C_out][4 C_in] (W_d[R][k]); stored transposed
+gs_status gs_net_set_weights(gs_net* nt, int layer, const void* w_host) {
+    if (!nt || layer < 0 || layer > 2 || !w_host) return GS_EINVAL;
+    int cin, cout;
+    layer_dims(nt->C, layer, &cin, &cout);
+    const int K = 4 * cin, R4 = 4 * cout;
+    const float2* src = (const float2*)w_host;
+    std::vector<float2> t((size_t)nt->nel[layer]);
+    for (int d = 0; d < 9; ++d)
+        for (int R = 0; R < R4; ++R)
+            for (int k = 0; k < K; ++k)
+                t[((size_t)d * K + k) * R4 + R] = src[((size_t)d * R4 + R) * K + k];
+    if (cudaMemcpy(nt->W[layer], t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return GS_ECUDA;
+    k_net_tobf16<<<grid_for(2 * nt->nel[layer], 256, 1024), 256>>>((const float*)nt->W[layer],
+                                                                   (__nv_bfloat16*)nt->Wb[layer],
+                                                                   2 * nt->nel[layer]);
+    const size_t b = (size_t)nt->nel[layer] * sizeof(float2);
+    cudaMemset(nt->m[layer], 0, b);
+    cudaMemset(nt->v[layer], 0, b);
+    nt->step = 0;
+    return cudaDeviceSynchronize() == cudaSuccess ? GS_OK : GS_ECUDA;
+}
+
+// what: 0 = FP32 weights, 1 = gradients of the last training step; layout as set
+gs_status gs_net_get(gs_net* nt, int what, int layer, void* host_out) {
+    if (!nt || layer < 0 || layer > 2 || !host_out || (what != 0 && what != 1)) return GS_EINVAL;
+    int cin, cout;
+    layer_dims(nt->C, layer, &cin, &cout);
+    const int K = 4 * cin, R4 = 4 * cout;
+    std::vector<float2> t((size_t)nt->nel[layer]);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(t.data(), what == 0 ? nt->W[layer] : nt->G[layer], t.size() * sizeof(float2),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GS_ECUDA;
+    float2* dst = (float2*)host_out;
+    for (int d = 0; d < 9; ++d)
+        for (int R = 0; R < R4; ++R)
+            for (int k = 0; k < K; ++k)
+                dst[((size_t)d * R4 + R) * K + k] = t[((size_t)d * K + k) * R4 + R];
+    return GS_OK;
+}
+
+gs_status gs_net_apply(gs_ctx* c, gs_net* nt, int type, int dir, int inverse, const void* t_dev,
+                       void* y_dev) {
+    if (!c || !nt) return GS_EINVAL;
+    if (!t_dev || !y_dev) return set_err(c, GS_EINVAL, "null vector");
+    if (!c->have_gauge) return set_err(c, GS_ENOGAUGE, "no gauge field set");
+    Plan* p = nullptr;
+    gs_status s = get_plan(c, type, dir, inverse, &p);
+    if (s != GS_OK) return s;
+    return net_apply_rest(c, nt, p, (const double2*)t_dev, (double2*)y_dev);
+}
+
+// One training step on `batch` pairs of the rest set of (type, dir, inverse):
+// t_dev, z_dev complex64 [batch][n_r][12] (z = D_rr^-1 t).  Loss = mean over
+// the batch of ||M(t)|_r - z||^2 / ||z||^2 (returned in *loss_out); the
+// gradients are left in the network; if update != 0 an Adam step with
+// learning rate lr follows (beta1 0.9, beta2 0.999, eps 1e-8).
+gs_status gs_net_train_step(gs_ctx* c, gs_net* nt, int type, int dir, int inverse, int batch,
+                            const void* t_dev, const void* z_dev, float lr, int update, float* loss_out) {
+    if (!c || !nt) return GS_EINVAL;
+    if (batch < 1 || !t_dev || !z_dev) return set_err(c, GS_EINVAL, "bad batch");
+    if (!c->have_gauge) return set_err(c, GS_ENOGAUGE, "no gauge field set");
+    Plan* p = nullptr;
+    gs_status s = get_plan(c, type, dir, inverse, &p);
+    if (s != GS_OK) return s;
+    if ((s = net_prepare(c, nt)) != GS_OK) return s;
+    const Plan* id = c->plans[0];
+    const int64_t V = c->V, nb = p->nb, nr = V - nb;
+    const int g = grid_for(nr * 12, 256, 1024);
+    const int blocks = (int)((V + kTS - 1) / kTS);
+    const float2* T = (const float2*)t_dev;
+    const float2* Z = (const float2*)z_dev;
+    double loss = 0.0;
+    for (int b = 0; b < batch; ++b) {
+        const float2* tb = T + (size_t)b * nr * 12;
+        const float2* zb = Z + (size_t)b * nr * 12;
+        GS_CUDA(c, cudaMemsetAsync(nt->act[0], 0, (size_t)V * 12 * sizeof(float2), c->stream));
+        k_net_embed32<<<g, 256, 0, c->stream>>>(tb, p->perm, nb, nr, nt->act[0]);
+        c->launches++;
+        if ((s = net_forward(c, nt, false)) != GS_OK) return s;
+        k_net_loss<<<g, 256, 0, c->stream>>>(nt->act[3], zb, p->perm, nb, nr, nt->red, nt->counter);
+        // gradient of the last activation into gact[0] (only 12 per site used)
+        GS_CUDA(c, cudaMemsetAsync(nt->gact[0], 0, (size_t)V * 12 * sizeof(float2), c->stream));
+        k_net_lossgrad<<<g, 256, 0, c->stream>>>(nt->act[3], zb, p->perm, nb, nr, nt->red,
+                                                 1.0f / batch, nt->gact[0]);
+        c->launches += 2;
+        GS_CUDA(c, cudaMemcpyAsync(nt->host_red, nt->red, 2 * sizeof(float), cudaMemcpyDeviceToHost,
+                                   c->stream));
+        // backward through the three layers
+        float2* gout = nt->gact[0];
+        float2* gin = nt->gact[1];
+        for (int l = 2; l >= 0; --l) {
+            int cin, cout;
+            layer_dims(nt->C, l, &cin, &cout);
+            gradw_dispatch(nt->C, cin, cout, nt->act[l], gout, nt->partial, nt->U32, id->nbr, V, c->stream);
+            k_net_reduce<<<grid_for(nt->nel[l], 256, 1024), 256, 0, c->stream>>>(nt->partial, nt->G[l],
+                                                                                 nt->nel[l], kChunks, b > 0);
+            c->launches += 2;
+            if (l > 0) {
+                k_net_wprime<<<grid_for(nt->nel[l], 256, 1024), 256, 0, c->stream>>>(nt->W[l], nt->Wp,
+                                                                                    4 * cin, 4 * cout);
+                conv_dispatch<float2>(nt->C, cout, cin, gout, gin, nt->Wp, nt->U32, id->nbr, V, blocks,
+                                      c->stream);
+                c->launches += 2;
+                float2* tmp = gout;
+                gout = gin;
+                gin = tmp;
+            }
+            GS_CHECK_LAUNCH(c);
+        }
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        loss += (double)nt->host_red[0] / (double)nt->host_red[1];
+    }
+    if (loss_out) *loss_out = (float)(loss / batch);
+    if (update) {
+        nt->step += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - powf(b1, (float)nt->step), c2 = 1.f - powf(b2, (float)nt->step);
+        for (int l = 0; l < 3; ++l) {
+            k_net_adam<<<grid_for(2 * nt->nel[l], 256, 1024), 256, 0, c->stream>>>(
+                (float*)nt->W[l], (const float*)nt->G[l], nt->m[l], nt->v[l], (__nv_bfloat16*)nt->Wb[l],
+                2 * nt->nel[l], lr, b1, b2, 1e-8f, c1, c2);
+            c->launches++;
+        }
+        GS_CHECK_LAUNCH(c);
+    }
+    return GS_OK;
+}
+
+gs_status gs_set_net(gs_ctx* c, gs_net* nt) {
+    if (!c) return GS_EINVAL;
+    c->net = nt;
+    return GS_OK;
+}
+
+}  // extern "C"
