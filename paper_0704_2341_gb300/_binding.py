@@ -385,6 +385,7 @@ class Context:
     def __init__(self, dims, m0, stream=None):
         self.dims = tuple(int(L) for L in dims)
         self.m0 = float(m0)
+        self.volume = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
         self.handle = gs_create(self.dims, self.m0, stream)
 
     def close(self):

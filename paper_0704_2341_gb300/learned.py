@@ -1,7 +1,8 @@
 """Training orchestration of the learned preconditioner (row A12).
 
 Every arithmetic step runs in the library's kernels: the training pairs come
-from the library's own inner solve (gs_solve_rr), the forward, backward and
+from the library's own inner solve (gs_solve_rr) or from its stencil
+(t = D_rr z for a given z), the forward, backward and
 Adam steps from gs_net_train_step.  This module only chooses the order of
 the samples (a seeded generator), moves vectors between the complex128
 solver layout and the complex64 training layout, and loops.
@@ -42,6 +43,32 @@ def make_pairs(torch, ctx, ptype, dir, inverse, sources, inner_tol=1e-8):
     return T.to(torch.complex64).contiguous(), Z.to(torch.complex64).contiguous()
 
 
+def make_pairs_apply(torch, ctx, ptype, dir, inverse, Z):
+    """Pairs (t, D_rr^-1 t) made the cheap way round: z is given (complex128
+    [n][n_r][12], numpy or device), t = D_rr z.  D_rr z is the rest part of
+    P D P^T [0; z] (the library's permute_sites and wilson_apply), so each
+    pair costs one stencil application instead of an inner solve.  With z
+    Gaussian the loss ||M t - z||^2 / ||z||^2 weighs every eigenmode of D_rr
+    alike, the small ones included.  Returns device complex64 T, Z."""
+    Zd = torch.as_tensor(np.ascontiguousarray(Z) if isinstance(Z, np.ndarray) else Z,
+                         device="cuda").to(torch.complex128)
+    n, nr = Zd.shape[0], Zd.shape[1]
+    V = ctx.volume
+    nb = V - nr
+    lab = torch.zeros((V, 12), dtype=torch.complex128, device="cuda")
+    site = torch.empty_like(lab)
+    dsite = torch.empty_like(lab)
+    dlab = torch.empty_like(lab)
+    T = torch.empty((n, nr, 12), dtype=torch.complex64, device="cuda")
+    for i in range(n):
+        lab[nb:] = Zd[i]
+        ctx.permute_sites(ptype, dir, inverse, 1, lab, site)
+        ctx.wilson_apply(site, dsite)
+        ctx.permute_sites(ptype, dir, inverse, 0, dsite, dlab)
+        T[i] = dlab[nb:]
+    return T, Zd.to(torch.complex64).contiguous()
+
+
 def train(torch, net, datasets, steps, batch, lr, seed):
     """datasets: list of (ctx, ptype, dir, inverse, T, Z).  Each step picks a
     data set and `batch` pairs with a seeded generator and runs one training
@@ -64,4 +91,4 @@ def fgmres_net_opts(**kw):
     return gs_default_opts(**o)
 
 
-__all__ = ["Net", "identity_like_weights", "make_pairs", "train", "fgmres_net_opts"]
+__all__ = ["Net", "identity_like_weights", "make_pairs", "make_pairs_apply", "train", "fgmres_net_opts"]
