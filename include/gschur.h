@@ -306,7 +306,8 @@ gs_status wilson_apply_lowp_multi(gs_ctx* ctx, int type, int dir, int inverse, i
  * S_bb on its own (opts->inner_tol, inner_prec, inner_solver as for
  * schur_solve).  t_dev, z_dev: complex128 [n_r][4][3] in label order (labels
  * n_b .. V-1).  Used, for example, to make the training pairs of the learned
- * preconditioner.  Synchronises the stream. */
+ * preconditioner.  stats->true_residual = ||t - D_rr z|| / ||t|| recomputed
+ * in FP64, inner_iters the Krylov steps taken.  Synchronises the stream. */
 gs_status gs_solve_rr(gs_ctx* ctx, int type, int dir, int inverse, const void* t_dev, void* z_dev,
                       const gs_solve_opts* opts, gs_solve_stats* stats);
 

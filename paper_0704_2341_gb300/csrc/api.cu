@@ -285,6 +285,7 @@ gs_status gs_solve_rr(gs_ctx* c, int type, int dir, int inverse, const void* t_d
     if (s == GS_OK) s = get_plan(c, type, dir, inverse, &p);
     if (s == GS_OK) {
         s = gs::inner_solve(c, p, (const double2*)t_dev, (double2*)z_dev, o, st);
+        st.true_residual = st.inner_residual;   // ||t - D_rr z|| / ||t||, recomputed in FP64
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess && s == GS_OK) s = set_err(c, GS_ECUDA, "gs_solve_rr: %s", cudaGetErrorString(e));
     }
