@@ -138,11 +138,15 @@ gs_status gs_set_gauge(gs_ctx* ctx, const void* U_dev);
  * direction (four partial sums combined in shared memory).  gs_get_option
  * returns the forced value, or under autotuning the variant chosen most
  * recently. */
-enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2 };
+enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 3 };
 /* GS_OPT_INNER_KERNEL: 0 = each inner BiCGStab solve runs as one persistent
  * cooperative kernel (grid barriers with bounded waits between its phases;
  * the default), 1 = five kernel launches per iteration with the convergence
- * flag read back while iterations are queued. */
+ * flag read back while iterations are queued.
+ * GS_OPT_NET_KERNEL: 0 = the C -> C layer of a 24-channel network runs on the
+ * tensor cores (tcgen05.mma, BF16 operands: the transported activations are
+ * rounded to BF16 as well as the weights; FP32 accumulation; the default),
+ * 1 = every layer on the CUDA cores (FP32 activations, BF16 weights). */
 gs_status gs_set_option(gs_ctx* ctx, int option, int value);
 gs_status gs_get_option(gs_ctx* ctx, int option, int* value);
 
@@ -334,7 +338,8 @@ gs_status gs_net_set_weights(gs_net* net, int layer, const void* w_host);
  * step; same layout as gs_net_set_weights (host memory). */
 gs_status gs_net_get(gs_net* net, int what, int layer, void* host_out);
 /* y = M t on the rest set; t_dev, y_dev complex128 [n_r][4][3] (label order).
- * Asynchronous. */
+ * BF16 weights; the C -> C layer as GS_OPT_NET_KERNEL selects.  Synchronises
+ * the stream; GS_TIMEOUT if the tensor-core layer gave up on a wait. */
 gs_status gs_net_apply(gs_ctx* ctx, gs_net* net, int type, int dir, int inverse,
                        const void* t_dev, void* y_dev);
 /* One training step on `batch` pairs: t_dev, z_dev complex64 [batch][n_r][4][3]

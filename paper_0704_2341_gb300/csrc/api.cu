@@ -186,6 +186,11 @@ gs_status gs_set_option(gs_ctx* c, int option, int value) {
         c->opt_inner_kernel = value;
         return GS_OK;
     }
+    if (option == GS_OPT_NET_KERNEL) {
+        if (value < 0 || value > 1) return set_err(c, GS_EINVAL, "network kernel %d not in 0..1", value);
+        c->opt_net_kernel = value;
+        return GS_OK;
+    }
     return set_err(c, GS_EINVAL, "unknown option %d", option);
 }
 
@@ -197,6 +202,10 @@ gs_status gs_get_option(gs_ctx* c, int option, int* value) {
     }
     if (option == GS_OPT_INNER_KERNEL) {
         *value = c->opt_inner_kernel;
+        return GS_OK;
+    }
+    if (option == GS_OPT_NET_KERNEL) {
+        *value = c->opt_net_kernel;
         return GS_OK;
     }
     return set_err(c, GS_EINVAL, "unknown option %d", option);

@@ -1,6 +1,7 @@
 // Internal declarations of the gschur CUDA library (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -196,6 +197,7 @@ struct gs_ctx {
     void* mixed = nullptr;             // mixed-precision state (mixed.cu)
     int opt_stencil_variant = 0;       // 0 = autotune, 1/3/4 = site (4/6/8 blocks), 2 = direction
     int opt_inner_kernel = 0;          // 0 = persistent cooperative BiCGStab, 1 = one launch per phase
+    int opt_net_kernel = 0;            // 0 = tensor-core C -> C layer (C = 24), 1 = CUDA cores only
     void* persist = nullptr;           // persistent-solver scratch (persistent.cu)
     void* multi = nullptr;             // multi-RHS workspaces (multi.cu)
     int coop_block_cap = 0;            // cap on cooperative grids (0 = whole GPU; batched solves)
@@ -311,6 +313,10 @@ struct LowpTables {
 gs_status lowp_tables(gs_ctx* c, const Plan* p, int prec, LowpTables* out);
 void free_multi(gs_ctx* c);
 void free_net_ctx(gs_ctx* c);
+size_t net_tc_weight_elems();
+gs_status net_tc_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw);
+gs_status net_conv_tc(gs_ctx* c, const float2* in, float2* out, const __nv_bfloat16* Bw, const float2* U32,
+                      const int2* nbr, int64_t V, int* err);
 gs_status inner_fgmres_net(gs_ctx* c, const Plan* p, const double2* r, double2* e, double tol,
                            int m, int* iters_out);
 void free_persist(gs_ctx* c);

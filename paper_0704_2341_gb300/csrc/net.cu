@@ -48,6 +48,10 @@ struct gs_net {
     float* red = nullptr;       // small reduction scratch
     unsigned int* counter = nullptr;
     float* host_red = nullptr;
+    __nv_bfloat16* Btc = nullptr;   // C -> C weights packed for the tensor cores (C = 24)
+    bool tc_dirty = true;           // Btc out of date with W[1]
+    int* tc_err = nullptr;          // mapped host word raised by the tensor-core kernel
+    int* tc_err_dev = nullptr;
 };
 
 namespace gs {
@@ -469,6 +473,17 @@ static gs_status net_forward(gs_ctx* c, gs_net* nt, bool bf16) {
     for (int l = 0; l < 3; ++l) {
         int cin, cout;
         layer_dims(nt->C, l, &cin, &cout);
+        if (bf16 && l == 1 && nt->Btc && c->opt_net_kernel == 0) {
+            gs_status s;
+            if (nt->tc_dirty) {
+                if ((s = net_tc_pack(c, nt->W[1], nt->Btc)) != GS_OK) return s;
+                nt->tc_dirty = false;
+            }
+            if ((s = net_conv_tc(c, nt->act[1], nt->act[2], nt->Btc, nt->U32, id->nbr, V, nt->tc_err_dev)) !=
+                GS_OK)
+                return s;
+            continue;
+        }
         if (bf16)
             conv_dispatch<__nv_bfloat162>(nt->C, cin, cout, nt->act[l], nt->act[l + 1], nt->Wb[l],
                                           nt->U32, id->nbr, V, blocks, c->stream);
@@ -494,6 +509,15 @@ gs_status net_apply_rest(gs_ctx* c, gs_net* nt, const Plan* p, const double2* t,
     k_net_restrict64<<<g, 256, 0, c->stream>>>(nt->act[3], p->perm, nb, nr, y);
     c->launches++;
     GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+// after a synchronisation: did a tensor-core layer give up on a wait?
+static gs_status net_check(gs_ctx* c, gs_net* nt) {
+    if (nt->tc_err && *(volatile int*)nt->tc_err) {
+        *(volatile int*)nt->tc_err = 0;
+        return set_err(c, GS_TIMEOUT, "tensor-core network layer: a wait timed out");
+    }
     return GS_OK;
 }
 
@@ -584,6 +608,7 @@ gs_status inner_fgmres_net(gs_ctx* c, const Plan* p, const double2* r, double2* 
         GS_CUDA(c, cudaMemcpyAsync(W.hbuf_host, W.hbuf, (2 * (m + 2) + 1) * sizeof(double2),
                                    cudaMemcpyDeviceToHost, c->stream));
         GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        if ((s = net_check(c, nt)) != GS_OK) return s;
         const double hn = sqrt(W.hbuf_host[2 * (m + 2)].x);
         if (!isfinite(hn)) return set_err(c, GS_NONFINITE, "non-finite FGMRES norm");
         for (int i = 0; i <= j; ++i)
@@ -667,7 +692,12 @@ gs_status gs_net_create(gs_net** out, int channels) {
          cudaMalloc(&nt->partial, (size_t)kChunks * big * sizeof(float2)) == cudaSuccess &&
          cudaMalloc(&nt->red, 4096 * sizeof(float)) == cudaSuccess &&
          cudaMalloc(&nt->counter, sizeof(unsigned int)) == cudaSuccess &&
-         cudaHostAlloc(&nt->host_red, 4 * sizeof(float), 0) == cudaSuccess;
+         cudaHostAlloc(&nt->host_red, 4 * sizeof(float), 0) == cudaSuccess &&
+         cudaHostAlloc(&nt->tc_err, sizeof(int), cudaHostAllocMapped) == cudaSuccess &&
+         cudaHostGetDevicePointer(&nt->tc_err_dev, nt->tc_err, 0) == cudaSuccess;
+    if (ok) *nt->tc_err = 0;
+    if (ok && channels == 24)
+        ok = cudaMalloc(&nt->Btc, net_tc_weight_elems() * sizeof(__nv_bfloat16)) == cudaSuccess;
     if (ok) ok = cudaMemset(nt->counter, 0, sizeof(unsigned int)) == cudaSuccess &&
                  cudaDeviceSynchronize() == cudaSuccess;
     if (!ok) {
@@ -697,6 +727,8 @@ gs_status gs_net_destroy(gs_net* nt) {
     cudaFree(nt->red);
     cudaFree(nt->counter);
     if (nt->host_red) cudaFreeHost(nt->host_red);
+    if (nt->tc_err) cudaFreeHost(nt->tc_err);
+    cudaFree(nt->Btc);
     cudaGetLastError();
     delete nt;
     return GS_OK;
@@ -723,6 +755,7 @@ gs_status gs_net_set_weights(gs_net* nt, int layer, const void* w_host) {
     cudaMemset(nt->m[layer], 0, b);
     cudaMemset(nt->v[layer], 0, b);
     nt->step = 0;
+    nt->tc_dirty = true;
     return cudaDeviceSynchronize() == cudaSuccess ? GS_OK : GS_ECUDA;
 }
 
@@ -753,7 +786,9 @@ gs_status gs_net_apply(gs_ctx* c, gs_net* nt, int type, int dir, int inverse, co
     Plan* p = nullptr;
     gs_status s = get_plan(c, type, dir, inverse, &p);
     if (s != GS_OK) return s;
-    return net_apply_rest(c, nt, p, (const double2*)t_dev, (double2*)y_dev);
+    if ((s = net_apply_rest(c, nt, p, (const double2*)t_dev, (double2*)y_dev)) != GS_OK) return s;
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return net_check(c, nt);
 }
 
 // One training step on `batch` pairs of the rest set of (type, dir, inverse):
@@ -828,6 +863,7 @@ gs_status gs_net_train_step(gs_ctx* c, gs_net* nt, int type, int dir, int invers
                 2 * nt->nel[l], lr, b1, b2, 1e-8f, c1, c2);
             c->launches++;
         }
+        nt->tc_dirty = true;
         GS_CHECK_LAUNCH(c);
     }
     return GS_OK;

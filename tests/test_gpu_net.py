@@ -156,3 +156,49 @@ def test_learned_gain_over_the_method_without_it(env):
         c.close()
     nt.close()
     untrained.close()
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 2, 4), (16, 16, 16, 4)])
+def test_tensor_core_layer_matches_cuda_cores_and_oracle(env, dims):
+    """The 24 -> 24 layer on the tensor cores (BF16 transported activations,
+    FP32 accumulation in tensor memory) against the CUDA-core path (FP32
+    activations, same BF16 weights) and the FP64 oracle.  (4,4,2,4): 384
+    GEMM rows, a ragged second tile; 16^3 x 4: 192 tiles, so CTAs run several
+    tiles and the pipeline's barrier phases carry across tiles."""
+    torch, gs = env
+    m0 = -0.2
+    V = li.volume(dims)
+    U = li.random_gauge(dims, 0.5, 8)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    perm, nb = permute.permutation(dims, 1)
+    nr = V - nb
+    Ws = [w.astype(np.complex64) for w in onet.init_weights(24, 11)]
+    nt = gs.Net(24)
+    for l, w in enumerate(Ws):
+        nt.set_weights(l, w)
+    t = li.gaussian_source(dims, 12).reshape(V, 12)[:nr]
+    td = to_dev(t, torch)
+    y_tc = torch.empty_like(td)
+    y_cc = torch.empty_like(td)
+    assert ctx.get_option(gs.GS_OPT_NET_KERNEL) == 0
+    nt.apply(ctx.handle, 1, 0, 0, td, y_tc)
+    ctx.set_option(gs.GS_OPT_NET_KERNEL, 1)
+    nt.apply(ctx.handle, 1, 0, 0, td, y_cc)
+    ctx.set_option(gs.GS_OPT_NET_KERNEL, 0)
+    torch.cuda.synchronize()
+    y_tc, y_cc = y_tc.cpu().numpy(), y_cc.cpu().numpy()
+    assert np.isfinite(y_tc).all()
+    # BF16 rounding of the transported activations only: ~1e-3 relative
+    assert rel(y_tc, y_cc) <= 5e-3
+    tfull = np.zeros((V, 12), complex)
+    tfull[perm[nb:]] = t
+    y = onet.forward([w.astype(np.complex128) for w in Ws], tfull.reshape(V, 4, 3),
+                     onet.transports(U, dims))[-1].reshape(V, 12)[perm[nb:]]
+    assert rel(y_tc, y) <= 1e-2
+    assert rel(y_cc, y) <= 1e-2
+    # repeated application is deterministic
+    y2 = torch.empty_like(td)
+    nt.apply(ctx.handle, 1, 0, 0, td, y2)
+    assert np.array_equal(y2.cpu().numpy(), y_tc)
+    nt.close()
+    ctx.close()
