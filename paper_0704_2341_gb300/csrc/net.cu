@@ -144,8 +144,11 @@ __device__ __forceinline__ void stage_tile(const float2* __restrict__ in, const 
 }
 
 // out[V][R4][3] = sum_d W_d T_d ; threads: one per output row (>= 32)
-template <int CIN, int COUT, class WT>
-__global__ void k_net_conv(const float2* __restrict__ in, float2* __restrict__ out, const WT* __restrict__ W,
+__device__ __forceinline__ void store_act(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void store_act(__nv_bfloat162* p, float2 v) { *p = __floats2bfloat162_rn(v.x, v.y); }
+
+template <int CIN, int COUT, class WT, class OT = float2>
+__global__ void k_net_conv(const float2* __restrict__ in, OT* __restrict__ out, const WT* __restrict__ W,
                            const float2* __restrict__ U32, const int2* __restrict__ nbr, int64_t V) {
     constexpr int K = 4 * CIN, R4 = 4 * COUT;
     __shared__ float2 T[K][kNCol];
@@ -172,10 +175,10 @@ __global__ void k_net_conv(const float2* __restrict__ in, float2* __restrict__ o
             for (int s = 0; s < kTS; ++s) {
                 const int64_t x = base + s;
                 if (x < V) {
-                    float2* dst = out + (x * R4 + R) * 3;
-                    dst[0] = acc[s * 3 + 0];
-                    dst[1] = acc[s * 3 + 1];
-                    dst[2] = acc[s * 3 + 2];
+                    OT* dst = out + (x * R4 + R) * 3;
+                    store_act(dst + 0, acc[s * 3 + 0]);
+                    store_act(dst + 1, acc[s * 3 + 1]);
+                    store_act(dst + 2, acc[s * 3 + 2]);
                 }
             }
         }
@@ -473,14 +476,23 @@ static gs_status net_forward(gs_ctx* c, gs_net* nt, bool bf16) {
     for (int l = 0; l < 3; ++l) {
         int cin, cout;
         layer_dims(nt->C, l, &cin, &cout);
-        if (bf16 && l == 1 && nt->Btc && c->opt_net_kernel == 0) {
+        const bool tc = bf16 && nt->Btc && c->opt_net_kernel == 0;
+        if (tc && l == 0) {
+            // the input of the tensor-core layer is kept in BF16 (in act[1]'s memory)
+            k_net_conv<1, 24, __nv_bfloat162, __nv_bfloat162><<<blocks, 96, 0, c->stream>>>(
+                nt->act[0], (__nv_bfloat162*)nt->act[1], nt->Wb[0], nt->U32, id->nbr, V);
+            c->launches++;
+            GS_CHECK_LAUNCH(c);
+            continue;
+        }
+        if (tc && l == 1) {
             gs_status s;
             if (nt->tc_dirty) {
                 if ((s = net_tc_pack(c, nt->W[1], nt->Btc)) != GS_OK) return s;
                 nt->tc_dirty = false;
             }
-            if ((s = net_conv_tc(c, nt->act[1], nt->act[2], nt->Btc, nt->U32, id->nbr, V, nt->tc_err_dev)) !=
-                GS_OK)
+            if ((s = net_conv_tc(c, (const __nv_bfloat162*)nt->act[1], nt->act[2], nt->Btc, nt->U32, id->nbr, V,
+                                 nt->tc_err_dev)) != GS_OK)
                 return s;
             continue;
         }

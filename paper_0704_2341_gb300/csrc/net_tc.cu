@@ -1,24 +1,27 @@
 // The C -> C layer of the learned preconditioner (C = 24) on the fifth-generation
 // tensor cores: tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in
-// tensor memory), weights moved by the bulk-copy engine, transported
-// activations staged into shared memory by the CTA's threads.
+// tensor memory), weights moved by the bulk-copy engine, neighbour
+// activations gathered by cp.async and transported by the CTA's threads.
 //
 // The layer  out(x)[R, a] = sum_d sum_k W_d[R, k] (U_d(x) in(x + d))[k, a]
 // is a real GEMM over rows p = 3 x + a (site, colour):
 //   A[p, k'] = Re / Im of T_d(x)[k, a],  T_d(x) = U_d(x) in(x + d)
 //   B[n', k'] = the real form of W_d:  out_re = W_re T_re - W_im T_im,
 //               out_im = W_im T_re + W_re T_im
-// with n' = 2 R + (re, im), k' = (d, half, 2 kk + (re, im)), k = 48 half + kk.
+// with n' = 2 R + (re, im), k' = (d, quarter, 2 kk + (re, im)), k = 24 quarter + kk.
 // M = 256 rows per tile (two 128-lane accumulators), N = 192, K = 9 x 192,
-// taken in 18 chunks of 96 (one transport, 48 input rows).  Operands are in
+// taken in 36 chunks of 48 (one transport, 24 input rows).  Operands are in
 // the no-swizzle K-major core-matrix layout: an 8-row x 16-byte core matrix
 // is 128 contiguous bytes, core matrices adjacent in K are 128 bytes apart
-// (leading byte offset), 8-row groups 1536 bytes apart (stride byte offset).
+// (leading byte offset), 8-row groups 768 bytes apart (stride byte offset).
+// The input activations are BF16 ([V][96][3] complex as bf16x2).
 //
-// Pipeline (two stages): for chunk j the threads build A_j while the tensor
-// core runs chunk j - 1; one thread starts the bulk copy of B_j and, after
-// the block barrier, issues the 12 MMAs of the chunk and commits them to the
-// stage's mbarrier.  Every wait is bounded (1 s of global time); on a
+// Pipeline per chunk j of a tile: cp.async gathers the raw neighbour rows and
+// links of chunk j + 1 (double-buffered) while the threads transport chunk j
+// into the A stage (double-buffered, reused once the tensor core has
+// committed the chunk two back); one thread moves B_j by a bulk copy and,
+// after the block barrier, issues the chunk's six MMAs and commits them to
+// the stage's mbarrier.  Every wait is bounded (1 s of global time); on a
 // timeout the kernel stops, frees its tensor memory and raises err.
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -31,13 +34,21 @@ namespace {
 constexpr int kRows = 256;                       // GEMM rows per tile
 constexpr int kRC = 96;                          // 4 C, C = 24
 constexpr int kN = 192;                          // real output columns
-constexpr int kKC = 96;                          // real K per chunk
-constexpr int kChunks = 18;                      // 9 transports x 2 halves
-constexpr uint32_t kSBO = (kKC / 8) * 128;       // 1536
-constexpr uint32_t kABytes = kRows * kKC * 2;    // 49152
-constexpr uint32_t kBBytes = kN * kKC * 2;       // 36864
+constexpr int kQ = 24;                           // input rows per chunk
+constexpr int kKC = 2 * kQ;                      // real K per chunk
+constexpr int kChunks = 36;                      // 9 transports x 4 quarters
+constexpr int kSites = 88;                       // site slots of a tile (at most 86 used)
+constexpr uint32_t kSBO = (kKC / 8) * 128;       // 768
+constexpr uint32_t kABytes = kRows * kKC * 2;    // 24576
+constexpr uint32_t kBBytes = kN * kKC * 2;       // 18432
+constexpr uint32_t kPStride = kQ * 3 * 4 + 16;   // 304: raw rows of one site (+16 against bank conflicts)
+constexpr uint32_t kPBytes = kSites * kPStride;  // 26752
+constexpr uint32_t kUBytes = kSites * 9 * 8;     // 6336
+// dynamic shared memory map (offsets from a 128-byte aligned base)
+constexpr uint32_t kOffA = 0, kOffB = 2 * kABytes, kOffP = kOffB + 2 * kBBytes, kOffU = kOffP + 2 * kPBytes,
+                   kOffY = kOffU + 2 * kUBytes, kSmemUsed = kOffY + 9 * kSites * 4;
+constexpr size_t kSmem = kSmemUsed + 128;
 constexpr int kThreads = 256;
-constexpr size_t kSmem = 2 * (size_t)(kABytes + kBBytes) + 256;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint64_t gtime() {
@@ -76,6 +87,13 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -83,12 +101,35 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(a) b
     return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 
+// raw rows (and links) of chunk j of the tile into raw buffer bi
+__device__ __forceinline__ void gather(unsigned char* base, int bi, int j, const __nv_bfloat162* __restrict__ in,
+                                       const float2* __restrict__ U32, int64_t xs0, int nsite) {
+    const int d = j >> 2, qt = j & 3;
+    const int* Y = (const int*)(base + kOffY) + d * kSites;
+    const uint32_t P = su32(base + kOffP + bi * kPBytes);
+    for (int i = threadIdx.x; i < nsite * 18; i += kThreads) {
+        const int sl = i / 18, pc = i - sl * 18;
+        const unsigned char* src = (const unsigned char*)(in + ((int64_t)Y[sl] * kRC + kQ * qt) * 3) + pc * 16;
+        cp_async16(P + sl * kPStride + pc * 16, src);
+    }
+    if (d > 0 && qt < 2) {  // links of transport d (quarters 2, 3 reuse buffers 0, 1)
+        const int mu = (d - 1) & 3;
+        const uint32_t Ub = su32(base + kOffU + bi * kUBytes);
+        for (int i = threadIdx.x; i < nsite * 9; i += kThreads) {
+            const int sl = i / 9, e = i - sl * 9;
+            const int64_t ls = d <= 4 ? xs0 + sl : (int64_t)Y[sl];
+            cp_async8(Ub + (sl * 9 + e) * 8, U32 + (ls * 4 + mu) * 9 + e);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
-    k_net_conv_tc(const float2* __restrict__ in, float2* __restrict__ out, const __nv_bfloat16* __restrict__ Bw,
-                  const float2* __restrict__ U32, const int2* __restrict__ nbr, int64_t V, int* err) {
+    k_net_conv_tc(const __nv_bfloat162* __restrict__ in, float2* __restrict__ out,
+                  const __nv_bfloat16* __restrict__ Bw, const float2* __restrict__ U32,
+                  const int2* __restrict__ nbr, int64_t V, int* err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    // stage s: A at base + s kABytes, B at base + 2 kABytes + s kBBytes
     __shared__ __align__(8) uint64_t bfull[2], mdone[2];
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -110,74 +151,89 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int64_t rows = 3 * V;
     const int64_t ntiles = (rows + kRows - 1) / kRows;
-    uint32_t g = 0;      // chunks issued so far (stage = g & 1, use = g >> 1)
+    uint32_t g = 0;  // chunks issued so far (stage = g & 1, use = g >> 1)
     int bad = 0;
     const int kq = lane & 3, sj = lane >> 2;
     for (int64_t tile = blockIdx.x; tile < ntiles && !bad; tile += gridDim.x) {
         const int64_t row0 = tile * kRows;
         const int64_t xs0 = row0 / 3;
+        const int off = (int)(row0 - 3 * xs0);
+        int64_t xl = (row0 + kRows - 1) / 3;
+        if (xl > V - 1) xl = V - 1;
+        const int nsite = (int)(xl - xs0 + 1);
+        // neighbour site of every (transport, site) of the tile
+        int* Y = (int*)(base + kOffY);
+        for (int i = tid; i < 9 * kSites; i += kThreads) {
+            const int d = i / kSites, sl = i - d * kSites;
+            if (sl < nsite) {
+                const int64_t x = xs0 + sl;
+                Y[i] = d == 0 ? (int)x : (d <= 4 ? __ldg(&nbr[x * 4 + d - 1].x) : __ldg(&nbr[x * 4 + d - 5].y));
+            }
+        }
+        __syncthreads();
+        gather(base, 0, 0, in, U32, xs0, nsite);
         for (int j = 0; j < kChunks; ++j, ++g) {
+            if (j + 1 < kChunks) {
+                gather(base, (j + 1) & 1, j + 1, in, U32, xs0, nsite);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            __syncthreads();
             const uint32_t s = g & 1u, u = g >> 1;
             if (g >= 2 && !mbar_wait(su32(&mdone[s]), (u - 1) & 1u)) bad = 1;
-            const int d = j >> 1, h = j & 1;
             if (tid == 0 && !bad) {
                 const uint32_t bar = su32(&bfull[s]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBBytes)
                              : "memory");
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        su32(base + 2 * kABytes + s * kBBytes)),
+                        su32(base + kOffB + s * kBBytes)),
                     "l"(Bw + (size_t)j * (kBBytes / 2)), "r"(kBBytes), "r"(bar)
                     : "memory");
             }
-            // A chunk: warp items = (group of 8 sites) x (group of 4 input rows)
-            unsigned char* a_s = base + s * kABytes;
-            for (int wi = warp; wi < 11 * 12; wi += kThreads / 32) {
-                const int sg = wi / 12, kg = wi - sg * 12;
-                const int64_t x = xs0 + 8 * sg + sj;
-                const int64_t r0 = 3 * x - row0;
+            // transport chunk j: warp items = (8 sites) x (4 input rows); lane = (site, row)
+            const int d = j >> 2, bi = j & 1;
+            const unsigned char* P = base + kOffP + bi * kPBytes;
+            const float2* Ub = (const float2*)(base + kOffU + bi * kUBytes);
+            unsigned char* a_s = base + kOffA + s * kABytes;
+            for (int wi = warp; wi < 11 * 6; wi += kThreads / 32) {
+                const int sg = wi / 6, kg = wi - sg * 6;
+                const int sl = 8 * sg + sj;
+                const int r0 = 3 * sl - off;
                 if (r0 >= kRows) continue;
-                const int kk = 4 * kg + kq, k = 48 * h + kk;
+                const int kk = 4 * kg + kq;
                 float2 t[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-                if (x < V) {
-                    int64_t y = x;
-                    const float2* uu = nullptr;
-                    bool dag = false;
-                    if (d >= 1 && d <= 4) {
-                        y = __ldg(&nbr[x * 4 + (d - 1)].x);
-                        uu = U32 + (x * 4 + (d - 1)) * 9;
-                    } else if (d >= 5) {
-                        y = __ldg(&nbr[x * 4 + (d - 5)].y);
-                        uu = U32 + (y * 4 + (d - 5)) * 9;
-                        dag = true;
-                    }
-                    const float2* src = in + (y * kRC + k) * 3;
-                    const float2 p0 = __ldg(src), p1 = __ldg(src + 1), p2 = __ldg(src + 2);
-                    if (!uu) {
+                if (sl < nsite) {
+                    const __nv_bfloat162* pr = (const __nv_bfloat162*)(P + sl * kPStride) + kk * 3;
+                    const float2 p0 = __bfloat1622float2(pr[0]), p1 = __bfloat1622float2(pr[1]),
+                                 p2 = __bfloat1622float2(pr[2]);
+                    if (d == 0) {
                         t[0] = p0;
                         t[1] = p1;
                         t[2] = p2;
-                    } else if (!dag) {
+                    } else if (d <= 4) {
+                        const float2* uu = Ub + sl * 9;
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
-                            const float2 q0 = cmul(__ldg(uu + 3 * a), p0), q1 = cmul(__ldg(uu + 3 * a + 1), p1),
-                                         q2 = cmul(__ldg(uu + 3 * a + 2), p2);
+                            const float2 q0 = cmul(uu[3 * a], p0), q1 = cmul(uu[3 * a + 1], p1),
+                                         q2 = cmul(uu[3 * a + 2], p2);
                             t[a] = make_float2(q0.x + q1.x + q2.x, q0.y + q1.y + q2.y);
                         }
                     } else {
+                        const float2* uu = Ub + sl * 9;
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
-                            const float2 q0 = cmulc(__ldg(uu + a), p0), q1 = cmulc(__ldg(uu + 3 + a), p1),
-                                         q2 = cmulc(__ldg(uu + 6 + a), p2);
+                            const float2 q0 = cmulc(uu[a], p0), q1 = cmulc(uu[3 + a], p1), q2 = cmulc(uu[6 + a], p2);
                             t[a] = make_float2(q0.x + q1.x + q2.x, q0.y + q1.y + q2.y);
                         }
                     }
                 }
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const int64_t r = r0 + a;
+                    const int r = r0 + a;
                     if (r >= 0 && r < kRows)
-                        *(__nv_bfloat162*)(a_s + core_off((int)r, 2 * kk)) = __floats2bfloat162_rn(t[a].x, t[a].y);
+                        *(__nv_bfloat162*)(a_s + core_off(r, 2 * kk)) = __floats2bfloat162_rn(t[a].x, t[a].y);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -190,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     bad = 1;
                 } else {
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t a0 = su32(base + s * kABytes), b0 = su32(base + 2 * kABytes + s * kBBytes);
+                    const uint32_t a0 = su32(base + kOffA + s * kABytes), b0 = su32(base + kOffB + s * kBBytes);
 #pragma unroll
                     for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -248,6 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.fence::before_thread_sync;");
         if (__syncthreads_or(bad)) bad = 1;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     if (bad && tid == 0) atomicExch(err, 1);
     // every committed MMA has been waited for on the normal path; after a
     // timeout give the in-flight ones a bounded time before freeing
@@ -268,9 +325,9 @@ __global__ void k_net_tc_pack(const float2* __restrict__ WT, __nv_bfloat16* __re
         const int chunk = (int)(e / (kN * kKC));
         const int rem = (int)(e - (int64_t)chunk * kN * kKC);
         const int np = rem / kKC, kp = rem - np * kKC;
-        const int d = chunk >> 1, h = chunk & 1;
+        const int d = chunk >> 2, qt = chunk & 3;
         const int o = np >> 1, cout = np & 1, kk = kp >> 1, cin = kp & 1;
-        const int k = 48 * h + kk;
+        const int k = kQ * qt + kk;
         const float2 w = WT[((int64_t)d * kRC + k) * kRC + o];
         const float v = cout == 0 ? (cin == 0 ? w.x : -w.y) : (cin == 0 ? w.y : w.x);
         Bw[(int64_t)chunk * (kBBytes / 2) + core_off(np, kp) / 2] = __float2bfloat16_rn(v);
@@ -288,7 +345,7 @@ gs_status net_tc_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw) {
     return GS_OK;
 }
 
-gs_status net_conv_tc(gs_ctx* c, const float2* in, float2* out, const __nv_bfloat16* Bw, const float2* U32,
+gs_status net_conv_tc(gs_ctx* c, const __nv_bfloat162* in, float2* out, const __nv_bfloat16* Bw, const float2* U32,
                       const int2* nbr, int64_t V, int* err) {
     GS_CUDA(c, cudaFuncSetAttribute(k_net_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     const int64_t ntiles = (3 * V + kRows - 1) / kRows;
