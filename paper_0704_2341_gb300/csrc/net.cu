@@ -185,6 +185,91 @@ __global__ void k_net_conv(const float2* __restrict__ in, OT* __restrict__ out, 
     }
 }
 
+// The C -> 1 layer weights first: W_d acts on (channel, spin) and U_d on
+// colour, so  out(x) = sum_d U_d(x) Phi_d(x + d)  with  Phi_d(y) = W_d in(y).
+// k_net_phi: Phi[y][d][R][b] = sum_k W_d[R, k] in(y)[k, b] for 16 sites per
+// block (their inputs staged in shared memory); thread = (d, R) x site pair.
+constexpr int kPhiSites = 16;
+__global__ void __launch_bounds__(288) k_net_phi(const float2* __restrict__ in, float2* __restrict__ phi,
+                                                 const __nv_bfloat162* __restrict__ W, int64_t V) {
+    constexpr int K = 96;
+    __shared__ float2 sp[kPhiSites][K * 3];
+    const int64_t x0 = (int64_t)blockIdx.x * kPhiSites;
+    for (int e = threadIdx.x; e < kPhiSites * K * 3; e += blockDim.x) {
+        const int sl = e / (K * 3), c = e - sl * (K * 3);
+        sp[sl][c] = (x0 + sl < V) ? in[(x0 + sl) * (K * 3) + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int dR = threadIdx.x % 36, sg = threadIdx.x / 36;
+    const int d = dR >> 2, R = dR & 3;
+    float2 acc[2][3];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) acc[q][b] = make_float2(0.f, 0.f);
+    const __nv_bfloat162* w = W + (int64_t)d * K * 4 + R;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+        const float2 wk = __bfloat1622float2(w[k * 4]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) cfma2(acc[q][b], wk, sp[sg + 8 * q][k * 3 + b]);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int64_t y = x0 + sg + 8 * q;
+        if (y < V) {
+            float2* dst = phi + ((y * 9 + d) * 4 + R) * 3;
+            dst[0] = acc[q][0];
+            dst[1] = acc[q][1];
+            dst[2] = acc[q][2];
+        }
+    }
+}
+
+// out(x)[R, a] = sum_d (U_d(x) Phi_d(x + d)[R])[a]; one thread per (site, R)
+__global__ void k_net_phi_gather(const float2* __restrict__ phi, float2* __restrict__ out,
+                                 const float2* __restrict__ U32, const int2* __restrict__ nbr, int64_t V) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V * 4; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i >> 2;
+        const int R = (int)(i & 3);
+        const float2* p0 = phi + ((x * 9) * 4 + R) * 3;
+        float2 acc[3] = {p0[0], p0[1], p0[2]};
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const int2 nb = __ldg(nbr + x * 4 + mu);
+            {   // +mu: U_mu(x) Phi_{1+mu}(x + mu)
+                const float2* p = phi + (((int64_t)nb.x * 9 + 1 + mu) * 4 + R) * 3;
+                const float2* u = U32 + (x * 4 + mu) * 9;
+                const float2 q0 = p[0], q1 = p[1], q2 = p[2];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cfma2(acc[a], __ldg(u + 3 * a), q0);
+                    cfma2(acc[a], __ldg(u + 3 * a + 1), q1);
+                    cfma2(acc[a], __ldg(u + 3 * a + 2), q2);
+                }
+            }
+            {   // -mu: U_mu(x - mu)^dag Phi_{5+mu}(x - mu)
+                const float2* p = phi + (((int64_t)nb.y * 9 + 5 + mu) * 4 + R) * 3;
+                const float2* u = U32 + ((int64_t)nb.y * 4 + mu) * 9;
+                const float2 q0 = p[0], q1 = p[1], q2 = p[2];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float2 c0 = __ldg(u + a), c1 = __ldg(u + 3 + a), c2 = __ldg(u + 6 + a);
+                    cfma2(acc[a], make_float2(c0.x, -c0.y), q0);
+                    cfma2(acc[a], make_float2(c1.x, -c1.y), q1);
+                    cfma2(acc[a], make_float2(c2.x, -c2.y), q2);
+                }
+            }
+        }
+        float2* dst = out + (x * 4 + R) * 3;
+        dst[0] = acc[0];
+        dst[1] = acc[1];
+        dst[2] = acc[2];
+    }
+}
+
 // partial[chunk][d][k][R] = sum over the chunk's sites and colours of
 // g_out(x)[R, a] conj(T_d(x)[k, a]);  grid = (kChunks, 9)
 template <int CIN, int COUT>
@@ -494,6 +579,16 @@ static gs_status net_forward(gs_ctx* c, gs_net* nt, bool bf16) {
             if ((s = net_conv_tc(c, (const __nv_bfloat162*)nt->act[1], nt->act[2], nt->Btc, nt->U32, id->nbr, V,
                                  nt->tc_err_dev)) != GS_OK)
                 return s;
+            continue;
+        }
+        if (tc && l == 2) {
+            // weights first; Phi ([V][9][4][3]) in the training gradient buffer
+            k_net_phi<<<(int)((V + kPhiSites - 1) / kPhiSites), 288, 0, c->stream>>>(nt->act[2], nt->gact[0],
+                                                                                  nt->Wb[2], V);
+            k_net_phi_gather<<<grid_for(V * 4, 256, c->num_sms * 8), 256, 0, c->stream>>>(nt->gact[0], nt->act[3],
+                                                                                      nt->U32, id->nbr, V);
+            c->launches += 2;
+            GS_CHECK_LAUNCH(c);
             continue;
         }
         if (bf16)
