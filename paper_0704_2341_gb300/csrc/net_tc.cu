@@ -48,7 +48,7 @@ constexpr uint32_t kUBytes = kSites * 9 * 8;     // 6336
 constexpr uint32_t kOffA = 0, kOffB = 2 * kABytes, kOffP = kOffB + 2 * kBBytes, kOffU = kOffP + 2 * kPBytes,
                    kOffY = kOffU + 2 * kUBytes, kSmemUsed = kOffY + 9 * kSites * 4;
 constexpr size_t kSmem = kSmemUsed + 128;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint64_t gtime() {
@@ -276,12 +276,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!bad) {
-            const int q = warp >> 2, wq = warp & 3;
+            // warp w reads lanes 32 (w % 4) .. + 31 of accumulator (w / 4) % 2, columns half w / 8
+            const int q = (warp >> 2) & 1, wq = warp & 3, ch = warp >> 3;
             const int r = 128 * q + 32 * wq + lane;
             const int64_t p = row0 + r;
             const int64_t x = p / 3;
             const int a = (int)(p - 3 * x);
-            for (int c = 0; c < kN; c += 32) {
+            for (int c = ch * (kN / 2); c < (ch + 1) * (kN / 2); c += 32) {
                 uint32_t v[32];
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
