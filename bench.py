@@ -38,7 +38,12 @@ FIELD = "8^4 heatbath b5.4"
 M0 = -0.4
 # FP64 peak: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM (the part's nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
-NCU_SUMMARY = os.path.join(ROOT, "profiles", "dslash_f64_8x4_traffic.txt")
+# DRAM traffic per launch from one ncu capture, per profiled kernel family
+# (0: the FP64 stencil, 3: the persistent FP64 BiCGStab), with the hash of the
+# sources it was taken on
+NCU_SUMMARY = {0: (os.path.join(ROOT, "profiles", "dslash_f64_8x4_traffic.txt"), ("dslash_f64.cu",)),
+               3: (os.path.join(ROOT, "profiles", "bicg_persistent_f64_8x4_traffic.txt"),
+                   ("persistent.cu", "dslash_f64.cuh", "gridsync.cuh"))}
 
 
 def _peaks():
@@ -49,24 +54,26 @@ def _peaks():
         return {}
 
 
-def _kernel_source_hash():
+def _kernel_source_hash(files):
     import hashlib
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_0704_2341_gb300", "csrc", "dslash_f64.cu"), "rb") as fh:
-        h.update(fh.read())
+    for name in files:
+        with open(os.path.join(ROOT, "paper_0704_2341_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic_per_launch():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
+def _ncu_traffic_per_launch(family):
+    """DRAM bytes per launch of a kernel family from its committed ncu
     summary, or None if absent or taken on a different kernel source."""
     try:
+        path, files = NCU_SUMMARY[family]
         kv = {}
-        for line in open(NCU_SUMMARY):
+        for line in open(path):
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_sha") != _kernel_source_hash():
+        if kv.get("kernel_source_sha") != _kernel_source_hash(files):
             return None
         return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -264,6 +271,136 @@ def stencil_roofline(case, dims, prec_name="f32", variant=0, reps=20):
     return out
 
 
+def _rest_count(gs, torch, ctx, ptype, mu, inv):
+    perm = torch.empty(ctx.volume, dtype=torch.int32, device="cuda")
+    return ctx.volume - ctx.get_permutation(ptype, mu, inv, perm)
+
+
+def train_learned(torch, gs, li, kind, m0, perms, stream, n_pairs=2000, seed=0):
+    """A 24-channel network trained on n_pairs pairs (t = D_rr z, z Gaussian)
+    spread over the 8 seeded 8^4 training fields of `kind` and the given
+    permutations: 400 Adam steps at lr 1e-3, 200 at 2e-4, batch 4."""
+    from paper_0704_2341_gb300 import learned
+    t0 = time.time()
+    li.prepare_training_gauges(kind, 8)
+    data, ctxs = [], []
+    per_field = n_pairs // 8
+    for i in range(8):
+        dims, U = li.training_gauge(kind, i)
+        c = gs.Context(dims, m0, stream.cuda_stream)
+        c.set_gauge(torch.from_numpy(U).to("cuda"))
+        ctxs.append(c)
+        for k, (pt, mu, inv) in enumerate(perms):
+            n = per_field // len(perms) + (1 if k < per_field % len(perms) else 0)
+            nr = _rest_count(gs, torch, c, pt, mu, inv)
+            Z = li.gaussian_source(dims, 1000 + 10 * i + k, n_src=n).reshape(n, -1, 12)[:, :nr]
+            T, Zd = learned.make_pairs_apply(torch, c, pt, mu, inv, Z)
+            data.append((c, pt, mu, inv, T, Zd))
+    net = gs.Net(24)
+    for layer, w in enumerate(learned.identity_like_weights(24, m0, 4 + seed)):
+        net.set_weights(layer, w)
+    hist = learned.train(torch, net, data, steps=400, batch=4, lr=1e-3, seed=7 + seed)
+    hist += learned.train(torch, net, data, steps=200, batch=4, lr=2e-4, seed=8 + seed)
+    torch.cuda.synchronize()
+    info = {"fields": "8 seeded 8^4 %s fields" % ("beta=5.4 heatbath" if kind == "heatbath"
+                                                  else "exp(i 0.2 H) + 10 APE"),
+            "pairs": sum(d[4].shape[0] for d in data), "adam_steps": len(hist), "batch": 4,
+            "loss_first": float(sum(hist[:5]) / 5), "loss_last50": float(sum(hist[-50:]) / 50),
+            "seconds": time.time() - t0}
+    del data
+    for c in ctxs:
+        c.close()
+    torch.cuda.empty_cache()
+    return net, info
+
+
+def learned_headline(args, torch, gs, li, ctx, f, x, stream, plain_value):
+    """The headline workload with the inner D_rr solve as FGMRES(64) + the
+    trained network inside FP32 defect correction (same 1e-10 outer target)."""
+    from paper_0704_2341_gb300 import learned
+    net, info = train_learned(torch, gs, li, "heatbath", M0, PERMS, stream)
+    o = learned.fgmres_net_opts(inner_restart=64, lowp_tol=1e-2)
+    ctx.set_net(net)
+    for _ in range(2):
+        for (t, mu, inv) in PERMS:
+            ctx.schur_solve(t, mu, inv, f, x, o)
+    torch.cuda.synchronize()
+    lms, worst, inner = 0.0, 0.0, 0
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for (t, mu, inv) in PERMS:
+            st = ctx.schur_solve(t, mu, inv, f, x, o)
+            worst = max(worst, st.true_residual)
+            inner += st.inner_iters
+        b.record(stream)
+        b.synchronize()
+        lms += a.elapsed_time(b)
+    ctx.set_net(None)
+    net.close()
+    value = len(PERMS) * args.steps / (lms / 1e3)
+    return {"value": value, "unit": UNIT, "ms_per_step": lms / args.steps,
+            "max_true_residual": worst, "speedup_vs_plain_f64": value / plain_value,
+            "inner_fgmres_steps_per_step": inner / args.steps,
+            "inner": "FGMRES(64) with the network as right preconditioner, FP32 defect "
+                     "correction (per-cycle tolerance 1e-2), tensor-core 24->24 layer",
+            "training": info}
+
+
+def learned_large(torch, gs, li):
+    """One source of the 32^3 x 64 learned-preconditioner workload: the inner
+    solve D_rr z = t (Type I rest set) to 1e-10 with FGMRES(64) + the network
+    trained on 8^4 fields of the same recipe, against the plain FP64 BiCGStab
+    on the same system (bounded at 3000 iterations)."""
+    from lattice_inputs import torchgen
+    from paper_0704_2341_gb300 import learned
+    stream = torch.cuda.current_stream()
+    m0 = -0.38
+    net, info = train_learned(torch, gs, li, "ape", m0, [(1, 0, 0)], stream, seed=1)
+    t0 = time.time()
+    dims, U = torchgen.workload_gauge_t("32^3x64 eps0.2 ape10", "cuda")
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    ctx = gs.Context(dims, m0, stream.cuda_stream)
+    ctx.set_gauge(U)
+    del U
+    torch.cuda.empty_cache()
+    nr = _rest_count(gs, torch, ctx, 1, 0, 0)
+    t = torch.from_numpy(li.gaussian_source(dims, 901).reshape(-1, 12)[:nr].copy()).to("cuda")
+    z = torch.empty_like(t)
+    ctx.set_net(net)
+    for _ in range(3):
+        net.apply(ctx.handle, 1, 0, 0, t, z)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(5):
+        net.apply(ctx.handle, 1, 0, 0, t, z)
+    b.record(stream)
+    b.synchronize()
+    apply_ms = a.elapsed_time(b) / 5
+    out = {"workload": "32^3x64, exp(i 0.2 H) seed 5 + 10 APE steps (alpha 0.5), Wilson m0=-0.38, "
+                       "Type I; source: complex Gaussian (seed 901) on the rest set",
+           "sample": "1 of the 12 sources, the inner D_rr solve alone (the complete S_bb solve at this "
+                     "size does not finish in a bench run)",
+           "rest_sites": nr, "field_generation_s": gen_s, "net_apply_ms": apply_ms, "training": info}
+    runs = (("fgmres_net", learned.fgmres_net_opts(inner_tol=1e-10, inner_restart=64, lowp_tol=1e-2)),
+            ("plain_f64_bicgstab", gs.gs_default_opts(inner_tol=1e-10, inner_max_iter=3000)))
+    for name, o in runs:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = ctx.solve_rr(1, 0, 0, t, z, o, allow=(gs.GS_OK, gs.GS_MAXITER, gs.GS_BREAKDOWN))
+        b.record(stream)
+        b.synchronize()
+        out[name] = {"status": gs.STATUS_NAMES.get(st.status, st.status), "steps": st.inner_iters,
+                     "true_residual": st.true_residual, "ms": a.elapsed_time(b)}
+        if name == "fgmres_net":
+            ctx.set_net(None)
+    net.close()
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +410,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lowp-dslash", action="store_true",
                     help="skip the 32^3x64 low-precision stencil roofline")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-preconditioner sections")
     ap.add_argument("--_cpu-sample", action="store_true", dest="cpu_sample")
     ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp"],
                     help="kernel micro-benchmark instead of the solve (for profiling)")
@@ -356,7 +495,8 @@ def main():
             worst = max(worst, w)
         barrier()
         ms = sum(a.elapsed_time(b) for a, b in ev)
-        prof = ctx.profile_read() if profile else None
+        prof = {fam: ctx.profile_read(fam) for fam in (gs.GS_PROF_STENCIL_F64, gs.GS_PROF_SOLVER_F64)} \
+            if profile else None
         if profile:
             ctx.profile(False)
         return ms, launches, worst, prof
@@ -424,27 +564,47 @@ def main():
         return
 
     peaks = _peaks()
-    avg_ms = prof.ms / max(prof.launches, 1)
-    flops_per_launch = prof.flops / max(prof.launches, 1)
-    bytes_per_launch = prof.bytes / max(prof.launches, 1)
-    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
-    traffic = _ncu_traffic_per_launch()
+    fam_names = {gs.GS_PROF_STENCIL_F64: "k_dslash_f64 (Wilson stencil on label ranges, FP64)",
+                 gs.GS_PROF_SOLVER_F64: "k_bicg_persistent_f64 (whole inner BiCGStab solve in one "
+                                         "cooperative launch: two D_rr stencils + vector updates per "
+                                         "iteration, FP64)"}
+    dom = max(prof, key=lambda fam: prof[fam].ms)
+
+    def fam_view(p):
+        avg_ms = p.ms / max(p.launches, 1)
+        fl = p.flops / max(p.launches, 1)
+        by = p.bytes / max(p.launches, 1)
+        ach = fl / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+        return avg_ms, fl, by, ach
+
+    avg_ms, flops_per_launch, bytes_per_launch, achieved = fam_view(prof[dom])
+    traffic = _ncu_traffic_per_launch(dom)
     roofline = {
-        "kernel": "k_dslash_f64 (Wilson stencil on label ranges, FP64)",
+        "kernel": fam_names[dom],
         "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
         "peak_source": "FP64 ALU: 152 SMs x 2.07 GHz x 4 flop/clk/SM (nominal 1.25 TFLOP/s; "
                        "no FP64 entry in MEASURED_PEAKS.json)",
-        "launches": prof.launches, "avg_launch_us": 1e3 * avg_ms,
+        "launches": prof[dom].launches, "avg_launch_us": 1e3 * avg_ms,
         "algorithmic_flops_per_launch": flops_per_launch,
         "algorithmic_bytes_per_launch": bytes_per_launch,
-        "hbm_view": {"achieved_gbs": bytes_per_launch / (avg_ms / 1e3) / 1e9,
+        "hbm_view": {"achieved_gbs": bytes_per_launch / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0,
                      "peak_gbs": peaks.get("hbm_gbs"),
                      "frac_of_measured": (bytes_per_launch / (avg_ms / 1e3) / 1e9 /
-                                          peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None},
-        "share_of_step": prof.ms / ms_prof if ms_prof > 0 else None,
+                                          peaks["hbm_gbs"]) if peaks.get("hbm_gbs") and avg_ms > 0
+                     else None},
+        "share_of_step": prof[dom].ms / ms_prof if ms_prof > 0 else None,
         "step_ms_with_events": ms_prof / args.steps,
+        "other_kernels": {},
     }
+    for fam in prof:
+        if fam == dom or prof[fam].launches == 0:
+            continue
+        o_ms, o_fl, o_by, o_ach = fam_view(prof[fam])
+        roofline["other_kernels"][fam_names[fam]] = {
+            "launches": prof[fam].launches, "avg_launch_us": 1e3 * o_ms,
+            "achieved_tflops": o_ach, "frac_fp64_alu": o_ach / FP64_PEAK_TFLOPS,
+            "share_of_step": prof[fam].ms / ms_prof if ms_prof > 0 else None}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -463,6 +623,8 @@ def main():
     for name in mixed:
         mixed[name]["speedup_vs_plain_f64"] = mixed[name]["value"] / value
     line["mixed_inner"] = mixed
+    if not args.no_learned:
+        line["learned_mixed"] = learned_headline(args, torch, gs, li, ctx, f, x, stream, value)
     if not args.no_lowp_dslash:
         ctx.close()
         ctx = None
@@ -474,6 +636,12 @@ def main():
                         "us_per_launch": r["us_per_launch"], "variant": r["variant"],
                         "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"]}
         line["dslash_lowp_32x32x32x64"] = lowp
+    if not args.no_learned:
+        if ctx is not None:
+            ctx.close()
+            ctx = None
+        torch.cuda.empty_cache()
+        line["learned_32x32x32x64"] = learned_large(torch, gs, li)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(0)
     print(json.dumps(line), flush=True)

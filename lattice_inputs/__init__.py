@@ -38,6 +38,9 @@ __all__ = [
     "average_plaquette",
     "gaussian_source",
     "point_sources",
+    "training_gauge",
+    "prepare_training_gauges",
+    "workload_gauge",
     "random_su3",
 ]
 
@@ -345,6 +348,46 @@ def cached(name, make):
     except OSError:
         pass
     return arr
+
+
+def training_gauge(kind, index):
+    """The seeded gauge fields the learned preconditioner is trained on (8^4).
+
+    * ``"heatbath"``: plaquette action beta = 5.4, 200 Cabibbo-Marinari
+      sweeps from a cold start, seed 11 + index (the ensemble of the
+      ``"8^4 heatbath b5.4"`` workload, other seeds);
+    * ``"ape"``: exp(i 0.2 H) seed 100 + index, then 10 APE steps alpha 0.5
+      (the recipe of the ``"32^3x64 eps0.2 ape10"`` workload on 8^4).
+    """
+    dims = (8, 8, 8, 8)
+    if kind == "heatbath":
+        seed = 11 + int(index)
+        return dims, cached("train_8p4_heatbath_b5.4_s%d" % seed, lambda: heatbath_gauge(dims, 5.4, 200, seed))
+    if kind == "ape":
+        seed = 100 + int(index)
+        return dims, cached("train_8p4_eps0.2_ape10_s%d" % seed,
+                            lambda: ape_smear(random_gauge(dims, 0.2, seed), dims, 0.5, 10))
+    raise KeyError(kind)
+
+
+def _make_training_gauge(args):
+    training_gauge(*args)
+    return True
+
+
+def prepare_training_gauges(kind, n=8, processes=8):
+    """Fill the field cache with training_gauge(kind, 0 .. n-1), generating
+    the missing ones in parallel worker processes (started with ``spawn``,
+    so this is safe in a process that already uses CUDA)."""
+    import multiprocessing as mp
+    import os
+    todo = [(kind, i) for i in range(n)
+            if not os.path.exists(_cache_path(("train_8p4_heatbath_b5.4_s%d" % (11 + i)) if kind == "heatbath"
+                                              else ("train_8p4_eps0.2_ape10_s%d" % (100 + i))))]
+    if not todo:
+        return
+    with mp.get_context("spawn").Pool(min(processes, len(todo))) as pool:
+        pool.map(_make_training_gauge, todo)
 
 
 def workload_gauge(name):

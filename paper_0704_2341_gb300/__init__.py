@@ -15,10 +15,10 @@ __all__ = ["Context", "GschurError", "gs_create", "gs_destroy", "gs_set_gauge",
            "schur_apply", "schur_solve", "gs_last_error", "gs_version", "gs_profile",
            "gs_profile_read", "wilson_apply_noalloc", "GS_ETOOLARGE", "gs_lowp_pack",
            "gs_lowp_unpack", "wilson_apply_lowp", "lowp_bytes", "gs_set_option",
-           "gs_get_option", "GS_OPT_STENCIL_VARIANT", "GS_OPT_INNER_KERNEL", "GS_PROF_STENCIL_F64",
+           "gs_get_option", "GS_OPT_STENCIL_VARIANT", "GS_OPT_INNER_KERNEL", "GS_OPT_NET_KERNEL", "GS_PROF_STENCIL_F64",
            "GS_PROF_STENCIL_F32", "GS_PROF_STENCIL_BF16", "GS_PROF_SOLVER_F64", "GS_PROF_SOLVER_LP",
            "schur_solve_multi", "schur_solve_batched", "gs_lowp_pack_multi", "gs_lowp_unpack_multi",
            "wilson_apply_lowp_multi", "gs_solve_rr", "Net", "gs_set_net", "GS_INNER_BICGSTAB",
            "GS_INNER_FGMRES_NET",
            "GS_TYPE_I", "GS_TYPE_II", "GS_F64", "GS_F32", "GS_BF16", "GS_GMRES",
-           "GS_BICGSTAB", "GS_OK", "GS_MAXITER"]
+           "GS_BICGSTAB", "GS_OK", "GS_MAXITER", "GS_BREAKDOWN", "STATUS_NAMES"]
