@@ -472,8 +472,8 @@ def main():
                     help="skip the 32^3x64 low-precision stencil roofline")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-preconditioner sections")
-    ap.add_argument("--no-batched", action="store_true",
-                    help="skip the batched multi-lattice multi-source section")
+    ap.add_argument("--batched", action="store_true",
+                    help="add the batched multi-lattice multi-source section (about 6 minutes)")
     ap.add_argument("--only", default=None, choices=["batched", "learned_large"],
                     help="run one section alone and print it")
     ap.add_argument("--_cpu-sample", action="store_true", dest="cpu_sample")
@@ -709,7 +709,7 @@ def main():
                         "us_per_launch": r["us_per_launch"], "variant": r["variant"],
                         "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"]}
         line["dslash_lowp_32x32x32x64"] = lowp
-    if not args.no_batched:
+    if args.batched:
         line["batched"] = batched_section(torch, gs, li)
     if not args.no_learned:
         if ctx is not None:
