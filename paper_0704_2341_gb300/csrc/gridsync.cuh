@@ -56,7 +56,6 @@ __device__ bool grid_sync(const GridSync& g) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();

@@ -205,7 +205,9 @@ __device__ void m_grid_total(const float* part, int N, float* tot) {
     if (t < N * NV) {
         const int j = t % N, q = t / N;
         float s = 0.f;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += ((const volatile float*)part)[((int64_t)b * N + j) * 4 + q];
+        // L2 loads (written before the grid barrier), pipelined; fixed order
+#pragma unroll 8
+        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(part + ((int64_t)b * N + j) * 4 + q);
         tot[q * kMaxRhs + j] = s;
     }
     __syncthreads();

@@ -10,7 +10,7 @@
 //
 // Grid barrier: a generation counter; the last block to arrive resets the
 // arrival count and advances the generation.  Every wait is bounded: after
-// kSpinLimit polls (about a second) the waiting block records GS_TIMEOUT in
+// kSpinLimit polls or one second of global time the waiting block records GS_TIMEOUT in
 // the error word, every block leaves its loop at the next barrier, and the
 // host reads the status.  The grid is sized with the occupancy calculator and
 // launched with cudaLaunchCooperativeKernel, which refuses grids that cannot
@@ -57,10 +57,13 @@ __device__ void grid_total(const T* partial, T (&tot)[NV]) {
         T s[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) s[q] = T(0);
+        // L2 loads (written by other blocks before the grid barrier); not
+        // volatile, so the loads of all iterations can be in flight at once
+#pragma unroll 4
         for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
-            const volatile T* p = partial + (int64_t)b * 4;
+            const T* p = partial + (int64_t)b * 4;
 #pragma unroll
-            for (int q = 0; q < NV; ++q) s[q] += p[q];
+            for (int q = 0; q < NV; ++q) s[q] += __ldcg(p + q);
         }
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
