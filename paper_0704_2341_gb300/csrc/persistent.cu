@@ -8,11 +8,11 @@
 // summing the per-block partials in the same fixed order, so all blocks hold
 // bit-identical scalars without another barrier.
 //
-// Grid barrier: a generation counter; the last block to arrive resets the
-// arrival count and advances the generation.  Every wait is bounded: after
-// kSpinLimit polls or one second of global time the waiting block records GS_TIMEOUT in
-// the error word, every block leaves its loop at the next barrier, and the
-// host reads the status.  The grid is sized with the occupancy calculator and
+// Grid barrier: one release add per block on an arrival counter that grows
+// through the launch, acquire polls until the barrier's last arrival (see
+// gridsync.cuh).  Every wait is bounded: after kSpinLimit polls or one second
+// of global time the waiting block records GS_TIMEOUT in the error word, the
+// other blocks leave when they see it, and the host reads the status.  The grid is sized with the occupancy calculator and
 // launched with cudaLaunchCooperativeKernel, which refuses grids that cannot
 // be co-resident.
 //
