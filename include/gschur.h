@@ -248,6 +248,14 @@ gs_status gs_profile(gs_ctx* ctx, int enable);
 enum { GS_PROF_STENCIL_F64 = 0, GS_PROF_STENCIL_F32 = 1, GS_PROF_STENCIL_BF16 = 2,
        GS_PROF_SOLVER_F64 = 3, GS_PROF_SOLVER_LP = 4 };
 gs_status gs_profile_read(gs_ctx* ctx, int family, gs_kernel_profile* out);
+/* SM clock cycles that block 0 of the persistent FP64 BiCGStab spent in each
+ * phase of its iterations while profiling was on (summed over launches):
+ * out[3 s + 0] = work of step s (s = 0: v = D p and <rhat, v>; 1: s = r - a v;
+ * 2: t = D s, <t, s>, <t, t>; 3: x, r updates, <rhat, r>, ||r||^2; 4: the
+ * p update), out[3 s + 1] = its grid barrier, out[3 s + 2] = the reduction of
+ * the per-block partials and the scalar algebra after it (0 for step 4).
+ * n >= 15.  A diagnostic of where an iteration's time goes; synchronises. */
+gs_status gs_profile_phases(gs_ctx* ctx, double* out, int n);
 
 /* Low-precision vectors and stencil: the arithmetic of the mixed inner solve
  * (GS_F32 / GS_BF16 storage, FP32 arithmetic, links stored as two rows of

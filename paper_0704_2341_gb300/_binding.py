@@ -34,7 +34,7 @@ EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson
            "gs_get_option", "schur_solve_multi", "schur_solve_batched", "gs_lowp_pack_multi",
            "gs_lowp_unpack_multi", "wilson_apply_lowp_multi", "gs_solve_rr", "gs_net_create",
            "gs_net_destroy", "gs_net_set_weights", "gs_net_get", "gs_net_apply",
-           "gs_net_train_step", "gs_set_net")
+           "gs_net_train_step", "gs_set_net", "gs_profile_phases")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -105,6 +105,7 @@ def _load():
         "gs_net_train_step": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, ctypes.c_float, i32,
                                     ctypes.POINTER(ctypes.c_float)]),
         "gs_set_net": (i32, [vp, vp]),
+        "gs_profile_phases": (i32, [vp, ctypes.POINTER(ctypes.c_double), i32]),
         "schur_solve_multi": (i32, [vp, i32, i32, i32, i32, vp, vp, ctypes.POINTER(gs_solve_opts),
                                     ctypes.POINTER(gs_solve_stats)]),
         "schur_solve_batched": (i32, [i32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
@@ -232,6 +233,13 @@ def wilson_apply_noalloc(dims, m0, U, x, y, stream=None):
 
 def gs_profile(ctx, enable):
     return _check(ctx, lib.gs_profile(ctx, int(bool(enable))))
+
+
+def gs_profile_phases(ctx):
+    """Cycles per phase of the persistent FP64 solver (block 0) while profiling was on."""
+    out = (ctypes.c_double * 15)()
+    _check(ctx, lib.gs_profile_phases(ctx, out, 15))
+    return list(out)
 
 
 def gs_profile_read(ctx, prec=GS_F64):
@@ -440,6 +448,9 @@ class Context:
 
     def profile_read(self, prec=GS_F64):
         return gs_profile_read(self.handle, prec)
+
+    def profile_phases(self):
+        return gs_profile_phases(self.handle)
 
     def solve_rr(self, ptype, dir, inverse, t, z, opts=None, allow=(GS_OK,)):
         return gs_solve_rr(self.handle, ptype, dir, inverse, t, z, opts, allow)

@@ -131,6 +131,11 @@ gs_status gs_destroy(gs_ctx* c) {
     free_net_ctx(c);
     free_mixed(c);
     free_persist(c);
+    for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
+    c->prof.ev.clear();
+    cudaFree(c->prof.ran_dev);
+    cudaFree(c->prof.phases_dev);
+    if (c->prof.ran_host) cudaFreeHost(c->prof.ran_host);
     for (Plan* p : c->plans) free_plan(p);
     c->plans.clear();
     cudaFree(c->U_abi);

@@ -130,6 +130,7 @@ struct Profiler {
     int* ran_dev = nullptr;           // per slot: 1 if the launch did work (not an early exit)
     int* ran_host = nullptr;          // pinned
     gs_kernel_profile tot[5] = {};    // stencil F64/F32/BF16, persistent solver F64 / low precision
+    unsigned long long* phases_dev = nullptr;  // [16] cycles per phase of the persistent FP64 solver
 };
 constexpr int kProfSlots = 2048;
 

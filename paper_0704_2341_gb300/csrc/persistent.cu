@@ -114,6 +114,32 @@ struct PArgs64 {
     double* partial;  // [6 slots][gridDim][4]
     GridSync sync;
     BicgState* st;
+    unsigned long long* phases;  // [16] or null: cycles per phase (block 0)
+};
+
+// phase clock of block 0 (profiling only)
+struct PhaseClock {
+    unsigned long long acc[15];
+    long long t;
+    bool on;
+    __device__ void start(bool enable) {
+        on = enable && blockIdx.x == 0 && threadIdx.x == 0;
+#pragma unroll
+        for (int i = 0; i < 15; ++i) acc[i] = 0;
+        t = on ? clock64() : 0;
+    }
+    __device__ __forceinline__ void mark(int i) {
+        if (on) {
+            const long long now = clock64();
+            acc[i] += (unsigned long long)(now - t);
+            t = now;
+        }
+    }
+    __device__ void flush(unsigned long long* out) {
+        if (on)
+#pragma unroll
+            for (int i = 0; i < 15; ++i) atomicAdd(out + i, acc[i]);
+    }
 };
 
 __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
@@ -154,6 +180,8 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
         }
         __syncthreads();
     }
+    PhaseClock pc;
+    pc.start(P.phases != nullptr);
     while (ok && !conv && status == GS_OK && iter < P.maxit) {
         // A: v = D p, <rhat, v> -> alpha
         {
@@ -163,7 +191,9 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 f64_tile<EPI_DOT_RHAT_V, true>(P.A, base, red, e0, e1, e2);
             double v[2] = {e0, e1};
             put_partial<2, double>(part + slot, v);
+            pc.mark(0);
             if (!(ok = grid_sync(P.sync))) break;
+            pc.mark(1);
             double tot[2];
             grid_total<2, double>(part + slot, tot);
             if (threadIdx.x == 0) {
@@ -175,6 +205,7 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 }
             }
             __syncthreads();
+            pc.mark(2);
             if (s_flag >= 10) {
                 status = s_flag - 10;
                 break;
@@ -197,9 +228,12 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 v[0] = fma(si.x, si.x, fma(si.y, si.y, v[0]));
             }
             put_partial<1, double>(part + 2 * slot, v);
+            pc.mark(3);
             if (!(ok = grid_sync(P.sync))) break;
+            pc.mark(4);
             double tot[1];
             grid_total<1, double>(part + 2 * slot, tot);
+            pc.mark(5);
             if (!isfinite(tot[0])) {
                 status = GS_NONFINITE;
                 break;
@@ -219,7 +253,9 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 f64_tile<EPI_DOT_TS, true>(P.C, base, red, e0, e1, e2);
             double v[3] = {e0, e1, e2};
             put_partial<3, double>(part + 3 * slot, v);
+            pc.mark(6);
             if (!(ok = grid_sync(P.sync))) break;
+            pc.mark(7);
             double tot[3];
             grid_total<3, double>(part + 3 * slot, tot);
             if (threadIdx.x == 0) {
@@ -228,6 +264,7 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 s_flag = (isfinite(sc[1].x) && isfinite(sc[1].y)) ? 0 : 10 + GS_NONFINITE;
             }
             __syncthreads();
+            pc.mark(8);
             if (s_flag >= 10) {
                 status = s_flag - 10;
                 break;
@@ -252,7 +289,9 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 v[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, v[2]));
             }
             put_partial<3, double>(part + 4 * slot, v);
+            pc.mark(9);
             if (!(ok = grid_sync(P.sync))) break;
+            pc.mark(10);
             double tot[3];
             grid_total<3, double>(part + 4 * slot, tot);
             ++iter;
@@ -275,6 +314,7 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 sc[3] = rho_new;
             }
             __syncthreads();
+            pc.mark(11);
         }
         // E: p = r + beta (p - omega v)
         {
@@ -289,9 +329,12 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 pi.y = fma(be.x, q.y, fma(be.y, q.x, ri.y));
                 P.p[i] = pi;
             }
+            pc.mark(12);
             if (!(ok = grid_sync(P.sync))) break;
+            pc.mark(13);
         }
     }
+    pc.flush(P.phases);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         BicgState* st = P.st;
         st->iter = iter;
@@ -654,6 +697,7 @@ gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs
     P.sync.gen = ps->words + 1;
     P.sync.err = (int*)(ps->words + 2);
     P.st = w.st;
+    P.phases = c->prof.on ? c->prof.phases_dev : nullptr;
     void* args[] = {&P};
     GS_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_bicg_persistent_f64, dim3(g),
                                            dim3(kPThreads), args, 0, c->stream));

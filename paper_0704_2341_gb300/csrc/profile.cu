@@ -106,7 +106,9 @@ gs_status gs_profile(gs_ctx* c, int enable) {
             for (auto& e : P.ev) GS_CUDA(c, cudaEventCreate(&e));
             GS_CUDA(c, cudaMalloc(&P.ran_dev, kProfSlots * sizeof(int)));
             GS_CUDA(c, cudaHostAlloc(&P.ran_host, kProfSlots * sizeof(int), 0));
+            GS_CUDA(c, cudaMalloc(&P.phases_dev, 16 * sizeof(unsigned long long)));
         }
+        GS_CUDA(c, cudaMemsetAsync(P.phases_dev, 0, 16 * sizeof(unsigned long long), c->stream));
         gs_status s = prof_harvest(c);
         if (s != GS_OK) return s;
         for (auto& t : P.tot) t = gs_kernel_profile{};
@@ -116,6 +118,20 @@ gs_status gs_profile(gs_ctx* c, int enable) {
         P.on = false;
         if (s != GS_OK) return s;
     }
+    return GS_OK;
+}
+
+gs_status gs_profile_phases(gs_ctx* c, double* out, int n) {
+    if (!c || !out || n < 15) return GS_EINVAL;
+    unsigned long long h[16] = {};
+    if (c->prof.phases_dev) {
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        GS_CUDA(c, cudaMemcpy(h, c->prof.phases_dev, sizeof h, cudaMemcpyDeviceToHost));
+    }
+    // marks: A work 0, sync 1, total 2; B work 3, sync 4, total 5; C 6, 7, 8;
+    // D 9, 10, 11; E work 12, sync 13
+    for (int i = 0; i < 14; ++i) out[i] = (double)h[i];
+    out[14] = 0.0;
     return GS_OK;
 }
 
