@@ -218,161 +218,5 @@ __device__ __forceinline__ void f64_tile(const StencilArgs& a, int64_t base,
     __syncthreads();
 }
 
-// One hop of direction MU for one site (FWD: U_mu(x) h_f, else U_mu(x-mu)^dag
-// h_b), as its contribution to the 24 doubles of hop_mu: up = g, lo =
-// X_mu^dag (-g) for the forward hop and X_mu^dag g for the backward one.
-template <int MU, bool FWD, bool CG>
-__device__ __forceinline__ void hop_one(const StencilArgs& a, int64_t j, bool valid, double2 (&up)[2][3],
-                                        double2 (&lo)[2][3]) {
-    double2 g[2][3];
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) g[s][c] = make_double2(0.0, 0.0);
-    if (valid) {
-        const int2 nb = __ldg(a.nbr + j * 4 + MU);
-        const int64_t l = FWD ? nb.x : nb.y;
-        const double2* src = nullptr;
-        if (l >= a.a0 && l < a.a1) src = a.inA + (l - a.a0) * kSiteC;
-        else if (l >= a.a1 && l < a.b1) src = a.inB + (l - a.a1) * kSiteC;
-        if (src) {
-            double2 p[12], u[9];
-            Half h;
-            load_spinor<CG>(src, p);
-            load_link(a.links + ((FWD ? j : l) * 4 + MU) * kLinkC, u);
-            project<MU, FWD>(p, h);
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    double2 t;
-                    if (FWD) {
-                        t = cmul(u[3 * r + 0], h.v[s][0]);
-                        cfma(t, u[3 * r + 1], h.v[s][1]);
-                        cfma(t, u[3 * r + 2], h.v[s][2]);
-                    } else {
-                        t = make_double2(0.0, 0.0);
-                        ccfma(t, u[0 + r], h.v[s][0]);
-                        ccfma(t, u[3 + r], h.v[s][1]);
-                        ccfma(t, u[6 + r], h.v[s][2]);
-                    }
-                    g[s][r] = t;
-                }
-        }
-    }
-    double2 d[2][3];
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            up[s][c] = g[s][c];
-            d[s][c] = FWD ? make_double2(-g[s][c].x, -g[s][c].y) : g[s][c];
-        }
-    xdag<MU>(d, lo);
-}
-
-// The tile of f64_tile for blocks of 8 warps (the persistent solver on small
-// rest sets, where a tile is alone on its SM and latency, not the FP64 pipe,
-// sets its time): warp w computes hop (w >> 2) of direction w & 3, so two
-// warps per SM sub-partition overlap their loads; the forward warps store
-// their partials, then the backward warps add theirs.  Phase 2: warp w sums
-// spin component w & 3, colours 0, 1 (w < 4) or colour 2 (w >= 4).
-template <int EPI, bool CG>
-__device__ __forceinline__ void f64_tile8(const StencilArgs& a, int64_t base,
-                                          double (&red)[4][24][kSitesPerBlock], double& e0, double& e1,
-                                          double& e2) {
-    const int warp = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    const int mu = warp & 3;
-    const bool fwd = warp < 4;
-    double2 up[2][3], lo[2][3];
-    {
-        const int64_t k = base + lane;
-        const bool valid = k < a.n_out;
-        const int64_t j = a.o0 + k;
-        switch (warp) {
-            case 0: hop_one<0, true, CG>(a, j, valid, up, lo); break;
-            case 1: hop_one<1, true, CG>(a, j, valid, up, lo); break;
-            case 2: hop_one<2, true, CG>(a, j, valid, up, lo); break;
-            case 3: hop_one<3, true, CG>(a, j, valid, up, lo); break;
-            case 4: hop_one<0, false, CG>(a, j, valid, up, lo); break;
-            case 5: hop_one<1, false, CG>(a, j, valid, up, lo); break;
-            case 6: hop_one<2, false, CG>(a, j, valid, up, lo); break;
-            default: hop_one<3, false, CG>(a, j, valid, up, lo); break;
-        }
-    }
-    if (fwd) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                red[mu][(s * 3 + c) * 2 + 0][lane] = up[s][c].x;
-                red[mu][(s * 3 + c) * 2 + 1][lane] = up[s][c].y;
-                red[mu][(6 + s * 3 + c) * 2 + 0][lane] = lo[s][c].x;
-                red[mu][(6 + s * 3 + c) * 2 + 1][lane] = lo[s][c].y;
-            }
-    }
-    __syncthreads();
-    if (!fwd) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                red[mu][(s * 3 + c) * 2 + 0][lane] += up[s][c].x;
-                red[mu][(s * 3 + c) * 2 + 1][lane] += up[s][c].y;
-                red[mu][(6 + s * 3 + c) * 2 + 0][lane] += lo[s][c].x;
-                red[mu][(6 + s * 3 + c) * 2 + 1][lane] += lo[s][c].y;
-            }
-    }
-    __syncthreads();
-    {
-        const int spin = warp & 3;
-        const int c0 = warp < 4 ? 0 : 2, c1 = warp < 4 ? 2 : 3;
-        const int64_t k = base + lane;
-        if (k < a.n_out) {
-            const int64_t j = a.o0 + k;
-            const double2* self = nullptr;
-            if (j >= a.a0 && j < a.a1) self = a.inA + (j - a.a0) * kSiteC;
-            else if (j >= a.a1 && j < a.b1) self = a.inB + (j - a.a1) * kSiteC;
-            double2* dst = a.out + k * kSiteC + spin * 3;
-            for (int c = c0; c < c1; ++c) {
-                const int q = (spin * 3 + c) * 2;
-                double re = red[0][q][lane] + red[1][q][lane] + red[2][q][lane] + red[3][q][lane];
-                double im = red[0][q + 1][lane] + red[1][q + 1][lane] + red[2][q + 1][lane] +
-                            red[3][q + 1][lane];
-                if (self) {
-                    const double2 sv = CG ? __ldcg(self + spin * 3 + c) : __ldg(self + spin * 3 + c);
-                    re = fma(a.diag, sv.x, re);
-                    im = fma(a.diag, sv.y, im);
-                }
-                if (a.negate) {
-                    re = -re;
-                    im = -im;
-                }
-                if (a.addend) {
-                    const double2 av = CG ? __ldcg(a.addend + k * kSiteC + spin * 3 + c)
-                                          : a.addend[k * kSiteC + spin * 3 + c];
-                    re += av.x;
-                    im += av.y;
-                }
-                dst[c] = make_double2(re, im);
-                if (EPI == EPI_DOT_RHAT_V) {
-                    const double2 rv = CG ? __ldcg(a.epi_vec + k * kSiteC + spin * 3 + c)
-                                          : a.epi_vec[k * kSiteC + spin * 3 + c];
-                    e0 = fma(rv.x, re, fma(rv.y, im, e0));
-                    e1 = fma(rv.x, im, fma(-rv.y, re, e1));
-                } else if (EPI == EPI_DOT_TS) {
-                    const double2 sv = CG ? __ldcg(a.epi_vec + k * kSiteC + spin * 3 + c)
-                                          : a.epi_vec[k * kSiteC + spin * 3 + c];
-                    e0 = fma(re, sv.x, fma(im, sv.y, e0));
-                    e1 = fma(re, sv.y, fma(-im, sv.x, e1));
-                    e2 = fma(re, re, fma(im, im, e2));
-                }
-            }
-        }
-    }
-    __syncthreads();
-}
-
 }  // namespace
 }  // namespace gs

@@ -26,14 +26,12 @@
 namespace gs {
 namespace {
 
-constexpr int kPThreads = 128;     // low-precision persistent solver
-constexpr int kP64Threads = 256;   // FP64 persistent solver (8-warp stencil tiles)
+constexpr int kPThreads = 128;
 
-// Sum NV values over the block (blockDim.x = 128 or 256; fixed pairwise
-// tree over the warps); thread 0 gets the result.
+// Sum NV values over the block (fixed tree); thread 0 gets the result.
 template <int NV, class T>
 __device__ void block_sum(T (&v)[NV], T (&out)[NV]) {
-    __shared__ T sm[8][4];
+    __shared__ T sm[kPThreads / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
@@ -44,13 +42,8 @@ __device__ void block_sum(T (&v)[NV], T (&out)[NV]) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const bool eight = blockDim.x > 128;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            T s4 = (sm[0][q] + sm[1][q]) + (sm[2][q] + sm[3][q]);
-            if (eight) s4 = s4 + ((sm[4][q] + sm[5][q]) + (sm[6][q] + sm[7][q]));
-            out[q] = s4;
-        }
+        for (int q = 0; q < NV; ++q) out[q] = (sm[0][q] + sm[1][q]) + (sm[2][q] + sm[3][q]);
     }
     __syncthreads();
 }
@@ -149,7 +142,7 @@ struct PhaseClock {
     }
 };
 
-__global__ void __launch_bounds__(kP64Threads) k_bicg_persistent_f64(PArgs64 P) {
+__global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
     __shared__ double red[4][24][kSitesPerBlock];
     __shared__ double2 sc[4];   // alpha, omega, beta, rho
     __shared__ int s_flag;       // 0, or 10 + a failure status
@@ -195,7 +188,7 @@ __global__ void __launch_bounds__(kP64Threads) k_bicg_persistent_f64(PArgs64 P) 
             double e0 = 0.0, e1 = 0.0, e2 = 0.0;
             for (int64_t base = (int64_t)blockIdx.x * kSitesPerBlock; base < P.A.n_out;
                  base += (int64_t)gridDim.x * kSitesPerBlock)
-                f64_tile8<EPI_DOT_RHAT_V, true>(P.A, base, red, e0, e1, e2);
+                f64_tile<EPI_DOT_RHAT_V, true>(P.A, base, red, e0, e1, e2);
             double v[2] = {e0, e1};
             put_partial<2, double>(part + slot, v);
             pc.mark(0);
@@ -257,7 +250,7 @@ __global__ void __launch_bounds__(kP64Threads) k_bicg_persistent_f64(PArgs64 P) 
             double e0 = 0.0, e1 = 0.0, e2 = 0.0;
             for (int64_t base = (int64_t)blockIdx.x * kSitesPerBlock; base < P.C.n_out;
                  base += (int64_t)gridDim.x * kSitesPerBlock)
-                f64_tile8<EPI_DOT_TS, true>(P.C, base, red, e0, e1, e2);
+                f64_tile<EPI_DOT_TS, true>(P.C, base, red, e0, e1, e2);
             double v[3] = {e0, e1, e2};
             put_partial<3, double>(part + 3 * slot, v);
             pc.mark(6);
@@ -622,9 +615,9 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_lp(PArgsLp P) {
 
 // co-resident grid for a cooperative launch: at most `want` blocks
 template <class K>
-static int coop_grid(gs_ctx* c, K kernel, int64_t want, int threads = kPThreads) {
+static int coop_grid(gs_ctx* c, K kernel, int64_t want) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPThreads, 0) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         return 0;
@@ -678,7 +671,7 @@ gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs
     if (s != GS_OK) return s;
     const int64_t tiles = (A.n_out + kSitesPerBlock - 1) / kSitesPerBlock;
     const int64_t want = tiles > (int64_t)c->num_sms ? tiles : (int64_t)c->num_sms;
-    const int g = coop_grid(c, k_bicg_persistent_f64, want, kP64Threads);
+    const int g = coop_grid(c, k_bicg_persistent_f64, want);
     if (g < 1) return set_err(c, GS_ECUDA, "no co-resident grid for the persistent solver");
     GS_CUDA(c, cudaMemsetAsync(ps->words, 0, 4 * sizeof(unsigned int), c->stream));
     PArgs64 P;
@@ -707,7 +700,7 @@ gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs
     P.phases = c->prof.on ? c->prof.phases_dev : nullptr;
     void* args[] = {&P};
     GS_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_bicg_persistent_f64, dim3(g),
-                                           dim3(kP64Threads), args, 0, c->stream));
+                                           dim3(kPThreads), args, 0, c->stream));
     c->launches++;
     return GS_OK;
 }
