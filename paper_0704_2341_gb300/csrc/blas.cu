@@ -19,6 +19,7 @@ namespace gs {
 namespace {
 
 constexpr int kBlas = 256;
+constexpr int kDotChunk = 8;   // vectors per block of the multi-dot
 
 // Block-reduce NV doubles; the last block gets the grand totals in thread 0.
 // Returns true (block-uniform) in the last block only.
@@ -212,42 +213,53 @@ __global__ void k_bicg_p(const double2* __restrict__ r, const double2* __restric
 // generic BLAS-1
 // ---------------------------------------------------------------------------
 
-// out[k] (+)= <X_k, y> = sum conj(X_k) y, k < nvec.  grid = (gx, nvec).
+// out[k] (+)= <X_k, y> = sum conj(X_k) y, k < nvec.  grid = (gx, ceil(nvec / 8)).
 __global__ void k_multidot(const double2* __restrict__ X, int64_t ld, const double2* __restrict__ y,
-                           int64_t n, double2* out, int accumulate, double* partial,
+                           int64_t n, int nvec, double2* out, int accumulate, double* partial,
                            unsigned int* counter) {
-    __shared__ double sm[kBlas / 32][2];
+    // block (bx, chunk): the dots of vectors 8 chunk .. 8 chunk + 7 with y over
+    // the block's strided range (y read once for eight vectors); the last
+    // block adds the per-block partials of every vector in block order
+    __shared__ double sm[kBlas / 32][2 * kDotChunk];
     __shared__ bool am_last;
-    const int k = blockIdx.y;
-    const double2* xk = X + (int64_t)k * ld;
-    double a0 = 0.0, a1 = 0.0;
+    const int k0 = blockIdx.y * kDotChunk;
+    const int nk = nvec - k0 < kDotChunk ? nvec - k0 : kDotChunk;
+    double a[2 * kDotChunk];
+#pragma unroll
+    for (int q = 0; q < 2 * kDotChunk; ++q) a[q] = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double2 u = xk[i], w = y[i];
-        a0 = fma(u.x, w.x, fma(u.y, w.y, a0));
-        a1 = fma(u.x, w.y, fma(-u.y, w.x, a1));
+        const double2 w = y[i];
+#pragma unroll
+        for (int q = 0; q < kDotChunk; ++q) {
+            if (q < nk) {
+                const double2 u = X[(int64_t)(k0 + q) * ld + i];
+                a[2 * q] = fma(u.x, w.x, fma(u.y, w.y, a[2 * q]));
+                a[2 * q + 1] = fma(u.x, w.y, fma(-u.y, w.x, a[2 * q + 1]));
+            }
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, off);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
-    }
-    if (lane == 0) {
-        sm[warp][0] = a0;
-        sm[warp][1] = a1;
+    for (int q = 0; q < 2 * kDotChunk; ++q) {
+        double v = a[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) sm[warp][q] = v;
     }
     __syncthreads();
     const unsigned nblocks = gridDim.x * gridDim.y;
     if (threadIdx.x == 0) {
-        double s0 = 0.0, s1 = 0.0;
-        for (int w = 0; w < nw; ++w) {
-            s0 += sm[w][0];
-            s1 += sm[w][1];
+        for (int q = 0; q < nk; ++q) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int w = 0; w < nw; ++w) {
+                s0 += sm[w][2 * q];
+                s1 += sm[w][2 * q + 1];
+            }
+            double* part = partial + ((int64_t)(k0 + q) * gridDim.x + blockIdx.x) * 2;
+            part[0] = s0;
+            part[1] = s1;
         }
-        double* part = partial + ((int64_t)k * gridDim.x + blockIdx.x) * 2;
-        part[0] = s0;
-        part[1] = s1;
         __threadfence();
         const unsigned prev = atomicAdd(counter, 1u);
         am_last = (prev == nblocks - 1);
@@ -255,12 +267,15 @@ __global__ void k_multidot(const double2* __restrict__ X, int64_t ld, const doub
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    for (int kk = threadIdx.x; kk < (int)gridDim.y; kk += blockDim.x) {
+    for (int kk = threadIdx.x; kk < nvec; kk += blockDim.x) {
         double s0 = 0.0, s1 = 0.0;
-        const volatile double* part = partial + (int64_t)kk * gridDim.x * 2;
+        const double* part = partial + (int64_t)kk * gridDim.x * 2;
+        // L2 loads of the partials (all written before the counter reached
+        // nblocks); independent, so they are in flight together
+#pragma unroll 8
         for (unsigned b = 0; b < gridDim.x; ++b) {
-            s0 += part[2 * b];
-            s1 += part[2 * b + 1];
+            s0 += __ldcg(part + 2 * b);
+            s1 += __ldcg(part + 2 * b + 1);
         }
         if (accumulate) {
             out[kk].x += s0;
@@ -364,8 +379,8 @@ gs_status launch_multidot(gs_ctx* c, RedScratch red, const double2* X, int64_t l
                           const double2* y, int64_t n, double2* dev_out, int accumulate) {
     if (nvec <= 0) return GS_OK;
     int gx = grid_for(n, kBlas, 64);
-    dim3 g(gx, nvec);
-    k_multidot<<<g, kBlas, 0, c->stream>>>(X, ld, y, n, dev_out, accumulate, red.partial,
+    dim3 g(gx, (nvec + kDotChunk - 1) / kDotChunk);
+    k_multidot<<<g, kBlas, 0, c->stream>>>(X, ld, y, n, nvec, dev_out, accumulate, red.partial,
                                            red.counter);
     c->launches++;
     GS_CHECK_LAUNCH(c);

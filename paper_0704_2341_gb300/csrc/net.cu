@@ -419,9 +419,11 @@ __global__ void k_net_loss(const float2* __restrict__ yfull, const float2* __res
     if (last && threadIdx.x == 0) {
         __threadfence();
         float s0 = 0.f, s1 = 0.f;
+        // L2 loads (written before the counter reached gridDim.x), in flight together
+#pragma unroll 8
         for (unsigned bl = 0; bl < gridDim.x; ++bl) {
-            s0 += ((volatile float*)red)[2 + 2 * bl];
-            s1 += ((volatile float*)red)[3 + 2 * bl];
+            s0 += __ldcg(red + 2 + 2 * bl);
+            s1 += __ldcg(red + 3 + 2 * bl);
         }
         red[0] = s0;
         red[1] = s1;
