@@ -378,8 +378,14 @@ gs_status launch_bicg_p_update(gs_ctx* c, InnerWork& w, int64_t n) {
 gs_status launch_multidot(gs_ctx* c, RedScratch red, const double2* X, int64_t ld, int nvec,
                           const double2* y, int64_t n, double2* dev_out, int accumulate) {
     if (nvec <= 0) return GS_OK;
-    int gx = grid_for(n, kBlas, 64);
-    dim3 g(gx, (nvec + kDotChunk - 1) / kDotChunk);
+    // enough blocks in flight to stream long vectors at HBM bandwidth, within
+    // the partial scratch (nvec x gx complex)
+    const int nchunks = (nvec + kDotChunk - 1) / kDotChunk;
+    int64_t cap = (int64_t)c->num_sms * 8 / nchunks;
+    if (cap < 64) cap = 64;
+    if (cap > kRedScratchDoubles / (2 * nvec)) cap = kRedScratchDoubles / (2 * nvec);
+    const int gx = grid_for(n, kBlas, (int)cap);
+    dim3 g(gx, nchunks);
     k_multidot<<<g, kBlas, 0, c->stream>>>(X, ld, y, n, nvec, dev_out, accumulate, red.partial,
                                            red.counter);
     c->launches++;

@@ -142,8 +142,9 @@ struct RedScratch {
 constexpr int kMaxRedBlocks = 1024;
 constexpr int kMaxRedVals = 8;
 constexpr int kMaxRestart = 64;
-// covers kMaxRedBlocks * kMaxRedVals and the multi-dot (64 blocks x 65 vectors x 2)
-constexpr int64_t kRedScratchDoubles = 16384;
+// covers kMaxRedBlocks * kMaxRedVals and the multi-dot (up to 1008 blocks per
+// vector x 65 vectors x 2)
+constexpr int64_t kRedScratchDoubles = 131072;
 
 // Inner-solver workspace (vectors of n_r sites).
 struct InnerWork {
