@@ -316,6 +316,9 @@ gs_status lowp_tables(gs_ctx* c, const Plan* p, int prec, LowpTables* out);
 void free_multi(gs_ctx* c);
 void free_net_ctx(gs_ctx* c);
 size_t net_tc_weight_elems();
+size_t net_phi_weight_elems();
+gs_status net_phi_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw);
+gs_status net_phi_tc(gs_ctx* c, const float2* in, float2* phi, const __nv_bfloat16* Bw, int64_t V, int* err);
 gs_status net_tc_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw);
 gs_status net_conv_tc(gs_ctx* c, const __nv_bfloat162* in, float2* out, const __nv_bfloat16* Bw, const float2* U32,
                       const int2* nbr, int64_t V, int* err);

@@ -49,6 +49,7 @@ struct gs_net {
     unsigned int* counter = nullptr;
     float* host_red = nullptr;
     __nv_bfloat16* Btc = nullptr;   // C -> C weights packed for the tensor cores (C = 24)
+    __nv_bfloat16* Bphi = nullptr;  // C -> 1 weights packed for the tensor cores (C = 24)
     bool tc_dirty = true;           // Btc out of date with W[1]
     int* tc_err = nullptr;          // mapped host word raised by the tensor-core kernel
     int* tc_err_dev = nullptr;
@@ -186,48 +187,8 @@ __global__ void k_net_conv(const float2* __restrict__ in, OT* __restrict__ out, 
 }
 
 // The C -> 1 layer weights first: W_d acts on (channel, spin) and U_d on
-// colour, so  out(x) = sum_d U_d(x) Phi_d(x + d)  with  Phi_d(y) = W_d in(y).
-// k_net_phi: Phi[y][d][R][b] = sum_k W_d[R, k] in(y)[k, b] for 16 sites per
-// block (their inputs staged in shared memory); thread = (d, R) x site pair.
-constexpr int kPhiSites = 16;
-__global__ void __launch_bounds__(288) k_net_phi(const float2* __restrict__ in, float2* __restrict__ phi,
-                                                 const __nv_bfloat162* __restrict__ W, int64_t V) {
-    constexpr int K = 96;
-    __shared__ float2 sp[kPhiSites][K * 3];
-    const int64_t x0 = (int64_t)blockIdx.x * kPhiSites;
-    for (int e = threadIdx.x; e < kPhiSites * K * 3; e += blockDim.x) {
-        const int sl = e / (K * 3), c = e - sl * (K * 3);
-        sp[sl][c] = (x0 + sl < V) ? in[(x0 + sl) * (K * 3) + c] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const int dR = threadIdx.x % 36, sg = threadIdx.x / 36;
-    const int d = dR >> 2, R = dR & 3;
-    float2 acc[2][3];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) acc[q][b] = make_float2(0.f, 0.f);
-    const __nv_bfloat162* w = W + (int64_t)d * K * 4 + R;
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-        const float2 wk = __bfloat1622float2(w[k * 4]);
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) cfma2(acc[q][b], wk, sp[sg + 8 * q][k * 3 + b]);
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int64_t y = x0 + sg + 8 * q;
-        if (y < V) {
-            float2* dst = phi + ((y * 9 + d) * 4 + R) * 3;
-            dst[0] = acc[q][0];
-            dst[1] = acc[q][1];
-            dst[2] = acc[q][2];
-        }
-    }
-}
-
+// colour, so  out(x) = sum_d U_d(x) Phi_d(x + d)  with  Phi_d(y) = W_d in(y);
+// Phi comes from the tensor-core kernel k_net_phi_tc (net_tc.cu).
 // out(x)[R, a] = sum_d (U_d(x) Phi_d(x + d)[R])[a]; one thread per (site, R)
 __global__ void k_net_phi_gather(const float2* __restrict__ phi, float2* __restrict__ out,
                                  const float2* __restrict__ U32, const int2* __restrict__ nbr, int64_t V) {
@@ -576,6 +537,7 @@ static gs_status net_forward(gs_ctx* c, gs_net* nt, bool bf16) {
             gs_status s;
             if (nt->tc_dirty) {
                 if ((s = net_tc_pack(c, nt->W[1], nt->Btc)) != GS_OK) return s;
+                if ((s = net_phi_pack(c, nt->W[2], nt->Bphi)) != GS_OK) return s;
                 nt->tc_dirty = false;
             }
             if ((s = net_conv_tc(c, (const __nv_bfloat162*)nt->act[1], nt->act[2], nt->Btc, nt->U32, id->nbr, V,
@@ -585,11 +547,11 @@ static gs_status net_forward(gs_ctx* c, gs_net* nt, bool bf16) {
         }
         if (tc && l == 2) {
             // weights first; Phi ([V][9][4][3]) in the training gradient buffer
-            k_net_phi<<<(int)((V + kPhiSites - 1) / kPhiSites), 288, 0, c->stream>>>(nt->act[2], nt->gact[0],
-                                                                                  nt->Wb[2], V);
+            gs_status s = net_phi_tc(c, nt->act[2], nt->gact[0], nt->Bphi, V, nt->tc_err_dev);
+            if (s != GS_OK) return s;
             k_net_phi_gather<<<grid_for(V * 4, 256, c->num_sms * 8), 256, 0, c->stream>>>(nt->gact[0], nt->act[3],
                                                                                       nt->U32, id->nbr, V);
-            c->launches += 2;
+            c->launches += 1;
             GS_CHECK_LAUNCH(c);
             continue;
         }
@@ -806,7 +768,8 @@ gs_status gs_net_create(gs_net** out, int channels) {
          cudaHostGetDevicePointer(&nt->tc_err_dev, nt->tc_err, 0) == cudaSuccess;
     if (ok) *nt->tc_err = 0;
     if (ok && channels == 24)
-        ok = cudaMalloc(&nt->Btc, net_tc_weight_elems() * sizeof(__nv_bfloat16)) == cudaSuccess;
+        ok = cudaMalloc(&nt->Btc, net_tc_weight_elems() * sizeof(__nv_bfloat16)) == cudaSuccess &&
+             cudaMalloc(&nt->Bphi, net_phi_weight_elems() * sizeof(__nv_bfloat16)) == cudaSuccess;
     if (ok) ok = cudaMemset(nt->counter, 0, sizeof(unsigned int)) == cudaSuccess &&
                  cudaDeviceSynchronize() == cudaSuccess;
     if (!ok) {
@@ -838,6 +801,7 @@ gs_status gs_net_destroy(gs_net* nt) {
     if (nt->host_red) cudaFreeHost(nt->host_red);
     if (nt->tc_err) cudaFreeHost(nt->tc_err);
     cudaFree(nt->Btc);
+    cudaFree(nt->Bphi);
     cudaGetLastError();
     delete nt;
     return GS_OK;

@@ -335,12 +335,208 @@ __global__ void k_net_tc_pack(const float2* __restrict__ WT, __nv_bfloat16* __re
     }
 }
 
+// ---------------------------------------------------------------------------
+// The C -> 1 layer, weights first, on the tensor cores:
+//   Phi[y][d][R][b] = sum_k W_d[R, k] in(y)[k, b]
+// a real GEMM over rows p = 3 y + b with K = 2 x 96 (k' = 2 k + (re, im)) and
+// N = 72 real outputs n' = 2 (4 d + R) + (re, im), padded to 80.  No
+// transport: the A rows are the site's own activations (FP32, contiguous),
+// converted to BF16 into the core-matrix layout.  128 rows per tile, one
+// 80-column accumulator; 78 KB of shared memory and 128 TMEM columns, so two
+// CTAs share an SM and overlap one's staging with the other's MMA/epilogue.
+// ---------------------------------------------------------------------------
+constexpr int kPhiRows = 128;
+constexpr int kPhiK = 192;
+constexpr int kPhiN = 80;
+constexpr int kPhiOut = 72;
+constexpr uint32_t kPhiSBO = (kPhiK / 8) * 128;          // 3072
+constexpr uint32_t kPhiABytes = kPhiRows * kPhiK * 2;    // 49152
+constexpr uint32_t kPhiBBytes = kPhiN * kPhiK * 2;       // 30720
+constexpr size_t kPhiSmem = kPhiABytes + kPhiBBytes + 128;
+constexpr int kPhiThreads = 256;
+constexpr uint32_t kPhiIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kPhiN >> 3) << 17) |
+                               ((uint32_t)(kPhiRows >> 4) << 24);
+
+__device__ __forceinline__ uint32_t phi_off(int r, int k) {
+    return (uint32_t)((r >> 3) * kPhiSBO + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+__device__ __forceinline__ uint64_t phi_desc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)(kPhiSBO >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+__global__ void __launch_bounds__(kPhiThreads, 2)
+    k_net_phi_tc(const float2* __restrict__ in, float2* __restrict__ phi, const __nv_bfloat16* __restrict__ Bw,
+                 int64_t V, int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    unsigned char* sA = base;
+    unsigned char* sB = base + kPhiABytes;
+    __shared__ __align__(8) uint64_t bfull, mdone;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bfull)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mdone)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(su32(&tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tslot;
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bfull)), "r"(kPhiBBytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         su32(sB)),
+                     "l"(Bw), "r"(kPhiBBytes), "r"(su32(&bfull))
+                     : "memory");
+    }
+    const int64_t rows = 3 * V;
+    const int64_t ntiles = (rows + kPhiRows - 1) / kPhiRows;
+    int bad = 0;
+    uint32_t used = 0;  // tiles whose MMAs this CTA committed
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t row0 = tile * kPhiRows;
+        const int64_t y0 = row0 / 3;
+        int64_t yl = (row0 + kPhiRows - 1) / 3;
+        if (yl > V - 1) yl = V - 1;
+        const int nsite = (int)(yl - y0 + 1);
+        const int off = (int)(row0 - 3 * y0);
+        // A: the tile's sites' activations, contiguous in memory ([y][k][b])
+        for (int e = tid; e < nsite * kRC * 3; e += kPhiThreads) {
+            const int b = e % 3, k = (e / 3) % kRC, sl = e / (3 * kRC);
+            const int r = 3 * sl + b - off;
+            if (r < 0 || r >= kPhiRows) continue;
+            const float2 v = __ldg(in + (y0 * kRC) * 3 + e);
+            *(__nv_bfloat162*)(sA + phi_off(r, 2 * k)) = __floats2bfloat162_rn(v.x, v.y);
+        }
+        // rows past the last site (the last tile only) are zero
+        for (int e = tid; e < kPhiRows * kRC; e += kPhiThreads) {
+            const int r = e / kRC, k = e - r * kRC;
+            if (row0 + r >= rows)
+                *(__nv_bfloat162*)(sA + phi_off(r, 2 * k)) = __floats2bfloat162_rn(0.f, 0.f);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            if ((used == 0 && !mbar_wait(su32(&bfull), 0u))) {
+                bad = 1;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+                for (int ks = 0; ks < kPhiK / 16; ++ks) {
+                    const uint64_t ad = phi_desc(su32(sA) + ks * 256);
+                    const uint64_t bd = phi_desc(su32(sB) + ks * 256);
+                    const uint32_t acc = ks > 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(kPhiIdesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&mdone))
+                             : "memory");
+            }
+        }
+        if (__syncthreads_or(bad)) {
+            bad = 1;
+            break;
+        }
+        ++used;
+        if (!mbar_wait(su32(&mdone), (used - 1) & 1u)) bad = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!__syncthreads_or(bad)) {
+            // warp w: lanes 32 (w % 4) .. + 31, columns 40 (w / 4) .. + 39
+            const int wq = warp & 3, ch = warp >> 2;
+            const int r = 32 * wq + lane;
+            const int64_t p = row0 + r;
+            const int64_t y = p / 3;
+            const int b = (int)(p - 3 * y);
+#pragma unroll
+            for (int c8 = 0; c8 < 5; ++c8) {
+                const int c = 40 * ch + 8 * c8;
+                uint32_t v[8];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                               "=r"(v[6]), "=r"(v[7])
+                             : "r"(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (p < rows) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int dR = c / 2 + i;
+                        if (dR < kPhiOut / 2)
+                            phi[(y * (kPhiOut / 2) + dR) * 3 + b] =
+                                make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                    }
+                }
+            }
+        } else {
+            bad = 1;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        if (__syncthreads_or(bad)) {
+            bad = 1;
+            break;
+        }
+    }
+    if (bad && tid == 0) atomicExch(err, 1);
+    // the weight copy must have landed before the CTA exits
+    if (tid == 0 && used == 0) mbar_wait(su32(&bfull), 0u);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
+// B of the C -> 1 layer from its FP32 master weights WT[d][k][R] (R < 4)
+__global__ void k_net_phi_pack(const float2* __restrict__ WT, __nv_bfloat16* __restrict__ Bw) {
+    const int n = kPhiN * kPhiK;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int np = e / kPhiK, kp = e - np * kPhiK;
+        float v = 0.f;
+        if (np < kPhiOut) {
+            const int o = np >> 1, cout = np & 1, k = kp >> 1, cin = kp & 1;
+            const int d = o >> 2, R = o & 3;
+            const float2 w = WT[((int64_t)d * kRC + k) * 4 + R];
+            v = cout == 0 ? (cin == 0 ? w.x : -w.y) : (cin == 0 ? w.y : w.x);
+        }
+        Bw[phi_off(np, kp) / 2] = __float2bfloat16_rn(v);
+    }
+}
+
 }  // namespace
 
 size_t net_tc_weight_elems() { return (size_t)kChunks * kN * kKC; }
 
 gs_status net_tc_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw) {
     k_net_tc_pack<<<grid_for((int64_t)net_tc_weight_elems(), 256, c->num_sms * 4), 256, 0, c->stream>>>(WT, Bw);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+size_t net_phi_weight_elems() { return (size_t)kPhiN * kPhiK; }
+
+gs_status net_phi_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw) {
+    k_net_phi_pack<<<grid_for(kPhiN * kPhiK, 256, 64), 256, 0, c->stream>>>(WT, Bw);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+gs_status net_phi_tc(gs_ctx* c, const float2* in, float2* phi, const __nv_bfloat16* Bw, int64_t V, int* err) {
+    GS_CUDA(c, cudaFuncSetAttribute(k_net_phi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPhiSmem));
+    const int64_t ntiles = (3 * V + kPhiRows - 1) / kPhiRows;
+    const int64_t cap = 2LL * c->num_sms;
+    const int grid = (int)(ntiles < cap ? ntiles : cap);
+    k_net_phi_tc<<<grid, kPhiThreads, kPhiSmem, c->stream>>>(in, phi, Bw, V, err);
     c->launches++;
     GS_CHECK_LAUNCH(c);
     return GS_OK;
