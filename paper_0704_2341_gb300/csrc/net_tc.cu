@@ -19,7 +19,7 @@
 // Pipeline per chunk j of a tile: cp.async gathers the raw neighbour rows and
 // links of chunk j + 1 (double-buffered) while the threads transport chunk j
 // into the A stage (double-buffered, reused once the tensor core has
-// committed the chunk two back); one thread moves B_j by a bulk copy and,
+// committed the chunk two back; a thread handles two input rows of one site); one thread moves B_j by a bulk copy and,
 // after the block barrier, issues the chunk's six MMAs and commits them to
 // the stage's mbarrier.  Every wait is bounded (1 s of global time); on a
 // timeout the kernel stops, frees its tensor memory and raises err.
@@ -124,6 +124,62 @@ __device__ __forceinline__ void gather(unsigned char* base, int bi, int j, const
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
+// Transport one chunk (24 input rows) of the raw rows in shared memory into
+// the A stage.  MODE 0: identity, 1: U_mu(x) p (forward hop), 2: U^dag p
+// (backward hop; the link is the neighbour's).  Warp items = (8 sites) x
+// (8 input rows); lane = (site j, row q) handles rows q and q + 4 of its
+// site with the link loaded once; the bf16x2 stores of a warp land in 32
+// distinct banks (bank = 4 (row mod 8) + q).
+template <int MODE>
+__device__ __forceinline__ void stage_chunk(const unsigned char* P, const float2* Ub, unsigned char* a_s, int warp,
+                                            int sj, int kq, int off, int nsite) {
+    for (int wi = warp; wi < 11 * 3; wi += kThreads / 32) {
+        const int sg = wi / 3, kg = wi - sg * 3;
+        const int sl = 8 * sg + sj;
+        const int r0 = 3 * sl - off;
+        if (r0 >= kRows) continue;
+        const bool have = sl < nsite;
+        float2 u[9];
+        if (MODE != 0 && have) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) u[e] = Ub[sl * 9 + e];
+        }
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int kk = 8 * kg + 4 * h2 + kq;
+            float2 t[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            if (have) {
+                const __nv_bfloat162* pr = (const __nv_bfloat162*)(P + sl * kPStride) + kk * 3;
+                const float2 p0 = __bfloat1622float2(pr[0]), p1 = __bfloat1622float2(pr[1]),
+                             p2 = __bfloat1622float2(pr[2]);
+                if (MODE == 0) {
+                    t[0] = p0;
+                    t[1] = p1;
+                    t[2] = p2;
+                } else if (MODE == 1) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float2 q0 = cmul(u[3 * a], p0), q1 = cmul(u[3 * a + 1], p1), q2 = cmul(u[3 * a + 2], p2);
+                        t[a] = make_float2(q0.x + q1.x + q2.x, q0.y + q1.y + q2.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float2 q0 = cmulc(u[a], p0), q1 = cmulc(u[3 + a], p1), q2 = cmulc(u[6 + a], p2);
+                        t[a] = make_float2(q0.x + q1.x + q2.x, q0.y + q1.y + q2.y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int r = r0 + a;
+                if (r >= 0 && r < kRows)
+                    *(__nv_bfloat162*)(a_s + core_off(r, 2 * kk)) = __floats2bfloat162_rn(t[a].x, t[a].y);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_net_conv_tc(const __nv_bfloat162* __restrict__ in, float2* __restrict__ out,
                   const __nv_bfloat16* __restrict__ Bw, const float2* __restrict__ U32,
@@ -192,50 +248,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     "l"(Bw + (size_t)j * (kBBytes / 2)), "r"(kBBytes), "r"(bar)
                     : "memory");
             }
-            // transport chunk j: warp items = (8 sites) x (4 input rows); lane = (site, row)
+            // transport chunk j into the A stage
             const int d = j >> 2, bi = j & 1;
             const unsigned char* P = base + kOffP + bi * kPBytes;
             const float2* Ub = (const float2*)(base + kOffU + bi * kUBytes);
             unsigned char* a_s = base + kOffA + s * kABytes;
-            for (int wi = warp; wi < 11 * 6; wi += kThreads / 32) {
-                const int sg = wi / 6, kg = wi - sg * 6;
-                const int sl = 8 * sg + sj;
-                const int r0 = 3 * sl - off;
-                if (r0 >= kRows) continue;
-                const int kk = 4 * kg + kq;
-                float2 t[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-                if (sl < nsite) {
-                    const __nv_bfloat162* pr = (const __nv_bfloat162*)(P + sl * kPStride) + kk * 3;
-                    const float2 p0 = __bfloat1622float2(pr[0]), p1 = __bfloat1622float2(pr[1]),
-                                 p2 = __bfloat1622float2(pr[2]);
-                    if (d == 0) {
-                        t[0] = p0;
-                        t[1] = p1;
-                        t[2] = p2;
-                    } else if (d <= 4) {
-                        const float2* uu = Ub + sl * 9;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            const float2 q0 = cmul(uu[3 * a], p0), q1 = cmul(uu[3 * a + 1], p1),
-                                         q2 = cmul(uu[3 * a + 2], p2);
-                            t[a] = make_float2(q0.x + q1.x + q2.x, q0.y + q1.y + q2.y);
-                        }
-                    } else {
-                        const float2* uu = Ub + sl * 9;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            const float2 q0 = cmulc(uu[a], p0), q1 = cmulc(uu[3 + a], p1), q2 = cmulc(uu[6 + a], p2);
-                            t[a] = make_float2(q0.x + q1.x + q2.x, q0.y + q1.y + q2.y);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const int r = r0 + a;
-                    if (r >= 0 && r < kRows)
-                        *(__nv_bfloat162*)(a_s + core_off(r, 2 * kk)) = __floats2bfloat162_rn(t[a].x, t[a].y);
-                }
-            }
+            if (d == 0) stage_chunk<0>(P, Ub, a_s, warp, sj, kq, off, nsite);
+            else if (d <= 4) stage_chunk<1>(P, Ub, a_s, warp, sj, kq, off, nsite);
+            else stage_chunk<2>(P, Ub, a_s, warp, sj, kq, off, nsite);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             if (__syncthreads_or(bad)) {
                 bad = 1;
@@ -408,12 +428,18 @@ __global__ void __launch_bounds__(kPhiThreads, 2)
         const int nsite = (int)(yl - y0 + 1);
         const int off = (int)(row0 - 3 * y0);
         // A: the tile's sites' activations, contiguous in memory ([y][k][b])
-        for (int e = tid; e < nsite * kRC * 3; e += kPhiThreads) {
-            const int b = e % 3, k = (e / 3) % kRC, sl = e / (3 * kRC);
-            const int r = 3 * sl + b - off;
-            if (r < 0 || r >= kPhiRows) continue;
-            const float2 v = __ldg(in + (y0 * kRC) * 3 + e);
-            *(__nv_bfloat162*)(sA + phi_off(r, 2 * k)) = __floats2bfloat162_rn(v.x, v.y);
+        // thread = (site, k): the three colours are three rows of the tile
+        for (int e = tid; e < nsite * kRC; e += kPhiThreads) {
+            const int sl = e / kRC, k = e - sl * kRC;
+            const float2* src = in + ((y0 + sl) * kRC + k) * 3;
+            const float2 v0 = __ldg(src), v1 = __ldg(src + 1), v2 = __ldg(src + 2);
+            const int r = 3 * sl - off;
+            if (r >= 0 && r < kPhiRows)
+                *(__nv_bfloat162*)(sA + phi_off(r, 2 * k)) = __floats2bfloat162_rn(v0.x, v0.y);
+            if (r + 1 >= 0 && r + 1 < kPhiRows)
+                *(__nv_bfloat162*)(sA + phi_off(r + 1, 2 * k)) = __floats2bfloat162_rn(v1.x, v1.y);
+            if (r + 2 < kPhiRows)
+                *(__nv_bfloat162*)(sA + phi_off(r + 2, 2 * k)) = __floats2bfloat162_rn(v2.x, v2.y);
         }
         // rows past the last site (the last tile only) are zero
         for (int e = tid; e < kPhiRows * kRC; e += kPhiThreads) {
