@@ -205,7 +205,7 @@ struct gs_ctx {
     int coop_block_cap = 0;            // cap on cooperative grids (0 = whole GPU; batched solves)
     struct gs_net* net = nullptr;      // learned preconditioner attached with gs_set_net (net.cu)
     bool net_links_fresh = false;      // the network's FP32 link copy matches U_abi
-    double2 *fg_V = nullptr, *fg_Z = nullptr, *fg_w = nullptr;  // FGMRES-net vectors
+    float2 *fg_V = nullptr, *fg_Z = nullptr, *fg_w = nullptr;  // FGMRES-net vectors (FP32 stencil layout)
     int64_t fg_cap = 0;
     int fg_m = 0;
     double2* fg_h = nullptr;           // device H column (2 (m+2) + 1)
@@ -315,6 +315,7 @@ struct LowpTables {
 gs_status lowp_tables(gs_ctx* c, const Plan* p, int prec, LowpTables* out);
 void free_multi(gs_ctx* c);
 void free_net_ctx(gs_ctx* c);
+gs_status lp_rr_apply_f32(gs_ctx* c, const Plan* p, const void* x, void* y);
 size_t net_tc_weight_elems();
 size_t net_phi_weight_elems();
 gs_status net_phi_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw);

@@ -796,6 +796,29 @@ static gs_status lp_entry(gs_ctx* c, int type, int dir, int inverse, int prec, L
     return lp_plan(c, p, prec, pd);
 }
 
+// y = D_rr x on the rest set of plan p, FP32 storage ([6][n_r] float4), the
+// autotuned stencil variant; for the FP32 flexible GMRES of the learned
+// preconditioner.
+gs_status lp_rr_apply_f32(gs_ctx* c, const Plan* p, const void* x, void* y) {
+    LpPlanData* pd = nullptr;
+    gs_status s = lp_plan(c, p, GS_F32, &pd);
+    if (s != GS_OK) return s;
+    LpArgs a;
+    memset(&a, 0, sizeof a);
+    a.out = y;
+    a.in = x;
+    a.links = pd->links;
+    a.nbr = pd->nbr_r;
+    a.n = pd->n;
+    a.diag = (float)(c->m0 + 4.0);
+    a.epi = EPI_NONE;
+    long long launches = 0;
+    s = launch_lp_stencil<float>(c, a, pd->hops, pd->variant, &launches);
+    c->launches += launches;
+    c->stencil_sites += pd->n;
+    return s;
+}
+
 }  // namespace gs
 
 using namespace gs;

@@ -338,6 +338,142 @@ __global__ void k_net_restrict64(const float2* __restrict__ full, const int32_t*
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 vectors of the flexible GMRES: the low-precision stencil's layout,
+// [6][n_r] float4 (float4 c of site k holds complexes 2c and 2c + 1), seen
+// by the BLAS below as n_r x 12 complex numbers in one consistent order.
+// ---------------------------------------------------------------------------
+constexpr int kFgBlas = 256;
+constexpr int kFgChunk = 8;
+
+// v = s r (FP64 AoS rest vector -> FP32 layout)
+__global__ void k_fg_pack(const double2* __restrict__ r, float4* __restrict__ v, int64_t nr, double sc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr * 6;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / nr, k = i - c * nr;
+        const double2 a = r[k * 12 + 2 * c], b = r[k * 12 + 2 * c + 1];
+        v[i] = make_float4((float)(sc * a.x), (float)(sc * a.y), (float)(sc * b.x), (float)(sc * b.y));
+    }
+}
+__global__ void k_fg_unpack(const float4* __restrict__ v, double2* __restrict__ r, int64_t nr) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr * 6;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / nr, k = i - c * nr;
+        const float4 a = v[i];
+        r[k * 12 + 2 * c] = make_double2(a.x, a.y);
+        r[k * 12 + 2 * c + 1] = make_double2(a.z, a.w);
+    }
+}
+// rest vector in the FP32 layout -> whole lattice (site order), zero on b
+__global__ void k_net_embed_lp(const float4* __restrict__ v, const int32_t* __restrict__ perm, int64_t nb,
+                               int64_t nr, float2* __restrict__ full) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr * 6;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / nr, k = i - c * nr;
+        const float4 a = v[i];
+        float2* dst = full + (int64_t)perm[nb + k] * 12 + 2 * c;
+        dst[0] = make_float2(a.x, a.y);
+        dst[1] = make_float2(a.z, a.w);
+    }
+}
+__global__ void k_net_restrict_lp(const float2* __restrict__ full, const int32_t* __restrict__ perm, int64_t nb,
+                                  int64_t nr, float4* __restrict__ v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr * 6;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / nr, k = i - c * nr;
+        const float2* src = full + (int64_t)perm[nb + k] * 12 + 2 * c;
+        const float2 a = src[0], b = src[1];
+        v[i] = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+// out[k] = <X_k, y> (k < nvec), FP32 products summed per thread, FP64 across
+// threads and blocks; block (bx, chunk) takes vectors 8 chunk .. + 7 against
+// one load of y; the last block adds the per-block partials in block order
+__global__ void k_fg_multidot(const float2* __restrict__ X, int64_t ld, const float2* __restrict__ y, int64_t n,
+                              int nvec, double2* out, double* partial, unsigned int* counter) {
+    __shared__ double sm[kFgBlas / 32][2 * kFgChunk];
+    __shared__ bool am_last;
+    const int k0 = blockIdx.y * kFgChunk;
+    const int nk = nvec - k0 < kFgChunk ? nvec - k0 : kFgChunk;
+    float a[2 * kFgChunk];
+#pragma unroll
+    for (int q = 0; q < 2 * kFgChunk; ++q) a[q] = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 w = y[i];
+#pragma unroll
+        for (int q = 0; q < kFgChunk; ++q) {
+            if (q < nk) {
+                const float2 u = X[(int64_t)(k0 + q) * ld + i];
+                a[2 * q] = fmaf(u.x, w.x, fmaf(u.y, w.y, a[2 * q]));
+                a[2 * q + 1] = fmaf(u.x, w.y, fmaf(-u.y, w.x, a[2 * q + 1]));
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 2 * kFgChunk; ++q) {
+        double v = (double)a[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) sm[warp][q] = v;
+    }
+    __syncthreads();
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < nk; ++q) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int w = 0; w < nw; ++w) {
+                s0 += sm[w][2 * q];
+                s1 += sm[w][2 * q + 1];
+            }
+            double* part = partial + ((int64_t)(k0 + q) * gridDim.x + blockIdx.x) * 2;
+            part[0] = s0;
+            part[1] = s1;
+        }
+        __threadfence();
+        am_last = atomicAdd(counter, 1u) == nblocks - 1;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    for (int kk = threadIdx.x; kk < nvec; kk += blockDim.x) {
+        double s0 = 0.0, s1 = 0.0;
+        const double* part = partial + (int64_t)kk * gridDim.x * 2;
+#pragma unroll 8
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            s0 += __ldcg(part + 2 * b);
+            s1 += __ldcg(part + 2 * b + 1);
+        }
+        out[kk] = make_double2(s0, s1);
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+// y += sign sum_k coef[k] X_k (coefficients FP64 on the device)
+__global__ void k_fg_multiaxpy(const float2* __restrict__ X, int64_t ld, int nvec, const double2* __restrict__ coef,
+                               float2* __restrict__ y, int64_t n, float sign) {
+    __shared__ float2 cf[kMaxRestart + 1];
+    for (int k = threadIdx.x; k < nvec; k += blockDim.x) {
+        const double2 c = coef[k];
+        cf[k] = make_float2(sign * (float)c.x, sign * (float)c.y);
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float2 acc = y[i];
+        for (int k = 0; k < nvec; ++k) {
+            const float2 c = cf[k], u = X[(int64_t)k * ld + i];
+            acc.x = fmaf(c.x, u.x, fmaf(-c.y, u.y, acc.x));
+            acc.y = fmaf(c.x, u.y, fmaf(c.y, u.x, acc.y));
+        }
+        y[i] = acc;
+    }
+}
+__global__ void k_fg_scale(const float2* __restrict__ x, float2* __restrict__ y, int64_t n, float a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = x[i];
+        y[i] = make_float2(a * v.x, a * v.y);
+    }
+}
+
 // loss of one sample: sums ||y_r - z||^2 and ||z||^2 into red[0..1]
 // (last-block pattern), then g_y = coef (y - z) on r, 0 on b
 __global__ void k_net_loss(const float2* __restrict__ yfull, const float2* __restrict__ z,
@@ -583,6 +719,44 @@ gs_status net_apply_rest(gs_ctx* c, gs_net* nt, const Plan* p, const double2* t,
     return GS_OK;
 }
 
+
+// host launchers of the FP32 FGMRES BLAS
+static gs_status fg_multidot(gs_ctx* c, const float2* X, int64_t ld, int nvec, const float2* y, int64_t n,
+                             double2* out) {
+    const int nchunks = (nvec + kFgChunk - 1) / kFgChunk;
+    int64_t cap = (int64_t)c->num_sms * 8 / nchunks;
+    if (cap < 64) cap = 64;
+    if (cap > kRedScratchDoubles / (2 * nvec)) cap = kRedScratchDoubles / (2 * nvec);
+    dim3 g(grid_for(n, kFgBlas, (int)cap), nchunks);
+    k_fg_multidot<<<g, kFgBlas, 0, c->stream>>>(X, ld, y, n, nvec, out, c->fg_red.partial, c->fg_red.counter);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+static gs_status fg_multiaxpy(gs_ctx* c, const float2* X, int64_t ld, int nvec, const double2* coef, float2* y,
+                              int64_t n, float sign) {
+    k_fg_multiaxpy<<<grid_for(n, kFgBlas, c->num_sms * 16), kFgBlas, 0, c->stream>>>(X, ld, nvec, coef, y, n, sign);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+// z = M(v) for rest vectors in the FP32 layout (BF16 weights)
+static gs_status net_apply_lp(gs_ctx* c, gs_net* nt, const Plan* p, const float4* v, float4* z) {
+    gs_status s = net_prepare(c, nt);
+    if (s != GS_OK) return s;
+    const int64_t V = c->V, nb = p->nb, nr = V - nb;
+    GS_CUDA(c, cudaMemsetAsync(nt->act[0], 0, (size_t)V * 12 * sizeof(float2), c->stream));
+    const int g = grid_for(nr * 6, 256, c->num_sms * 8);
+    k_net_embed_lp<<<g, 256, 0, c->stream>>>(v, p->perm, nb, nr, nt->act[0]);
+    c->launches++;
+    if ((s = net_forward(c, nt, true)) != GS_OK) return s;
+    k_net_restrict_lp<<<g, 256, 0, c->stream>>>(nt->act[3], p->perm, nb, nr, z);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
 // after a synchronisation: did a tensor-core layer give up on a wait?
 static gs_status net_check(gs_ctx* c, gs_net* nt) {
     if (nt->tc_err && *(volatile int*)nt->tc_err) {
@@ -592,15 +766,20 @@ static gs_status net_check(gs_ctx* c, gs_net* nt) {
     return GS_OK;
 }
 
-// Flexible GMRES(m) for D_rr e = r (FP64 vectors) with the network as right
-// preconditioner: z_j = M(v_j), w = D_rr z_j, CGS2, Givens on the host;
-// e = sum_j z_j y_j.  Stops at ||r - D_rr e|| <= tol ||r|| (estimate).
+// Flexible GMRES(m) for D_rr e = r with the network as right preconditioner,
+// in FP32: it is one cycle of the FP64 defect correction, which only asks it
+// to reduce the residual by the cycle tolerance and recomputes the true
+// residual in FP64 afterwards.  Vectors in the low-precision stencil's FP32
+// layout: v_0 = r / ||r||; z_j = M(v_j), w = D_rr z_j (FP32 stencil), CGS2
+// with FP32 products and FP64 sums, Givens rotations on the host;
+// e = sum_j z_j y_j (returned in FP64).  Stops at the estimate
+// ||r - D_rr e|| <= tol ||r||.
 gs_status inner_fgmres_net(gs_ctx* c, const Plan* p, const double2* r, double2* e, double tol,
                            int m, int* iters_out) {
     gs_net* nt = c->net;
     if (!nt) return set_err(c, GS_EINVAL, "no network attached (gs_set_net)");
     const int64_t nb = p->nb, nr = c->V - nb, n = nr * kSiteC;
-    const size_t vb = (size_t)n * sizeof(double2);
+    const size_t vb = (size_t)n * sizeof(float2);
     if (m < 1) m = 1;
     if (m > kMaxRestart) m = kMaxRestart;
     if (c->fg_cap < nr || c->fg_m < m) {
@@ -630,64 +809,55 @@ gs_status inner_fgmres_net(gs_ctx* c, const Plan* p, const double2* r, double2* 
         GS_CUDA(c, cudaMemsetAsync(c->fg_red.counter, 0, sizeof(unsigned int), c->stream));
     }
     gs_status s;
-    struct {
-        double2* hbuf;
-        double2* hbuf_host;
-        double2* y;
-        double2* y_host;
-        RedScratch red;
-    } W = {c->fg_h, c->fg_h_host, c->fg_y, c->fg_y_host, c->fg_red};
-    double2 *V = c->fg_V, *Z = c->fg_Z, *w = c->fg_w;
-    // beta = ||r||, v0 = r / beta
-    if ((s = launch_norm2(c, W.red, r, n, c->scal_dev)) != GS_OK) return s;
+    float2* V = c->fg_V;
+    float2* Z = c->fg_Z;
+    float2* w = c->fg_w;
+    double2* hbuf = (double2*)c->fg_h;
+    double2* hbuf_host = (double2*)c->fg_h_host;
+    // beta = ||r|| (FP64), v_0 = r / beta
+    if ((s = launch_norm2(c, c->fg_red, r, n, c->scal_dev)) != GS_OK) return s;
     GS_CUDA(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     const double beta = sqrt(c->scal_host[0]);
-    GS_CUDA(c, cudaMemsetAsync(e, 0, vb, c->stream));
     *iters_out = 0;
-    if (!(beta > 0.0)) return isfinite(beta) ? GS_OK : set_err(c, GS_NONFINITE, "non-finite FGMRES rhs");
-    if ((s = launch_scale_copy(c, r, V, n, 1.0 / beta)) != GS_OK) return s;
+    if (!(beta > 0.0)) {
+        GS_CUDA(c, cudaMemsetAsync(e, 0, (size_t)n * sizeof(double2), c->stream));
+        return isfinite(beta) ? GS_OK : set_err(c, GS_NONFINITE, "non-finite FGMRES rhs");
+    }
+    const int g6 = grid_for(nr * 6, 256, c->num_sms * 8);
+    k_fg_pack<<<g6, 256, 0, c->stream>>>(r, (float4*)V, nr, 1.0 / beta);
+    c->launches++;
     using cplx = std::complex<double>;
-    std::vector<cplx> H((size_t)(m + 1) * m), g(m + 1, 0.0), cs(m), sn(m);
-    g[0] = beta;
-    StencilArgs a;
-    memset(&a, 0, sizeof a);
-    a.o0 = nb;
-    a.n_out = nr;
-    a.a0 = nb;
-    a.a1 = c->V;
-    a.b1 = c->V;
-    a.diag = c->m0 + 4.0;
-    a.plan = p;
-    a.nbr = p->nbr;
-    a.links = p->links;
+    std::vector<cplx> H((size_t)(m + 1) * m), gv(m + 1, 0.0), cs(m), sn(m);
+    gv[0] = beta;
     int k = 0;
     for (int j = 0; j < m; ++j) {
-        double2* Vj = V + (size_t)j * n;
-        double2* Zj = Z + (size_t)j * n;
-        if ((s = net_apply_rest(c, nt, p, Vj, Zj)) != GS_OK) return s;
-        a.out = w;
-        a.inA = Zj;
-        if ((s = launch_stencil_f64(c, a)) != GS_OK) return s;
-        double2* h = W.hbuf;
-        double2* h2 = W.hbuf + (m + 2);
-        if ((s = launch_multidot(c, W.red, V, n, j + 1, w, n, h, 0)) != GS_OK) return s;
-        if ((s = launch_multiaxpy(c, V, n, j + 1, h, w, n, -1)) != GS_OK) return s;
-        if ((s = launch_multidot(c, W.red, V, n, j + 1, w, n, h2, 0)) != GS_OK) return s;
-        if ((s = launch_multiaxpy(c, V, n, j + 1, h2, w, n, -1)) != GS_OK) return s;
-        if ((s = launch_norm2(c, W.red, w, n, (double*)(W.hbuf + 2 * (m + 2)))) != GS_OK) return s;
-        GS_CUDA(c, cudaMemcpyAsync(W.hbuf_host, W.hbuf, (2 * (m + 2) + 1) * sizeof(double2),
-                                   cudaMemcpyDeviceToHost, c->stream));
+        float2* Vj = V + (size_t)j * n;
+        float2* Zj = Z + (size_t)j * n;
+        if ((s = net_apply_lp(c, nt, p, (const float4*)Vj, (float4*)Zj)) != GS_OK) return s;
+        if ((s = lp_rr_apply_f32(c, p, Zj, w)) != GS_OK) return s;
+        double2* h = hbuf;
+        double2* h2 = hbuf + (m + 2);
+        double2* hn2 = hbuf + 2 * (m + 2);
+        if ((s = fg_multidot(c, V, n, j + 1, w, n, h)) != GS_OK) return s;
+        if ((s = fg_multiaxpy(c, V, n, j + 1, h, w, n, -1.f)) != GS_OK) return s;
+        if ((s = fg_multidot(c, V, n, j + 1, w, n, h2)) != GS_OK) return s;
+        if ((s = fg_multiaxpy(c, V, n, j + 1, h2, w, n, -1.f)) != GS_OK) return s;
+        if ((s = fg_multidot(c, w, n, 1, w, n, hn2)) != GS_OK) return s;
+        GS_CUDA(c, cudaMemcpyAsync(hbuf_host, hbuf, (2 * (m + 2) + 1) * sizeof(double2), cudaMemcpyDeviceToHost,
+                                   c->stream));
         GS_CUDA(c, cudaStreamSynchronize(c->stream));
         if ((s = net_check(c, nt)) != GS_OK) return s;
-        const double hn = sqrt(W.hbuf_host[2 * (m + 2)].x);
+        const double hn = sqrt(hbuf_host[2 * (m + 2)].x);
         if (!isfinite(hn)) return set_err(c, GS_NONFINITE, "non-finite FGMRES norm");
         for (int i = 0; i <= j; ++i)
-            H[(size_t)i * m + j] = cplx(W.hbuf_host[i].x + W.hbuf_host[m + 2 + i].x,
-                                        W.hbuf_host[i].y + W.hbuf_host[m + 2 + i].y);
+            H[(size_t)i * m + j] = cplx(hbuf_host[i].x + hbuf_host[m + 2 + i].x, hbuf_host[i].y + hbuf_host[m + 2 + i].y);
         H[(size_t)(j + 1) * m + j] = hn;
-        if (hn > 0.0)
-            if ((s = launch_scale_copy(c, w, V + (size_t)(j + 1) * n, n, 1.0 / hn)) != GS_OK) return s;
+        if (hn > 0.0) {
+            k_fg_scale<<<grid_for(n, kFgBlas, c->num_sms * 16), kFgBlas, 0, c->stream>>>(w, V + (size_t)(j + 1) * n, n,
+                                                                                       (float)(1.0 / hn));
+            c->launches++;
+        }
         for (int i = 0; i < j; ++i) {
             const cplx h0 = H[(size_t)i * m + j], h1 = H[(size_t)(i + 1) * m + j];
             H[(size_t)i * m + j] = std::conj(cs[i]) * h0 + std::conj(sn[i]) * h1;
@@ -699,20 +869,26 @@ gs_status inner_fgmres_net(gs_ctx* c, const Plan* p, const double2* r, double2* 
         sn[j] = hh > 0.0 ? bb / hh : cplx(0.0);
         H[(size_t)j * m + j] = hh;
         H[(size_t)(j + 1) * m + j] = 0.0;
-        g[j + 1] = -sn[j] * g[j];
-        g[j] = std::conj(cs[j]) * g[j];
+        gv[j + 1] = -sn[j] * gv[j];
+        gv[j] = std::conj(cs[j]) * gv[j];
         k = j + 1;
-        if (std::abs(g[j + 1]) <= tol * beta || hn == 0.0) break;
+        if (std::abs(gv[j + 1]) <= tol * beta || hn == 0.0) break;
     }
     std::vector<cplx> y(k);
     for (int i = k - 1; i >= 0; --i) {
-        cplx acc = g[i];
+        cplx acc = gv[i];
         for (int l = i + 1; l < k; ++l) acc -= H[(size_t)i * m + l] * y[l];
         y[i] = acc / H[(size_t)i * m + i];
     }
-    for (int i = 0; i < k; ++i) W.y_host[i] = make_double2(y[i].real(), y[i].imag());
-    GS_CUDA(c, cudaMemcpyAsync(W.y, W.y_host, k * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
-    if ((s = launch_multiaxpy(c, Z, n, k, W.y, e, n, +1)) != GS_OK) return s;
+    double2* yh = (double2*)c->fg_y_host;
+    for (int i = 0; i < k; ++i) yh[i] = make_double2(y[i].real(), y[i].imag());
+    GS_CUDA(c, cudaMemcpyAsync(c->fg_y, yh, k * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    // e = sum_j z_j y_j, accumulated in w (FP32), returned in FP64
+    GS_CUDA(c, cudaMemsetAsync(w, 0, vb, c->stream));
+    if ((s = fg_multiaxpy(c, Z, n, k, (const double2*)c->fg_y, w, n, 1.f)) != GS_OK) return s;
+    k_fg_unpack<<<g6, 256, 0, c->stream>>>((const float4*)w, e, nr);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     *iters_out = k;
     return GS_OK;
@@ -728,7 +904,8 @@ void free_net_ctx(gs_ctx* c) {
     cudaFree(c->fg_red.counter);
     if (c->fg_h_host) cudaFreeHost(c->fg_h_host);
     if (c->fg_y_host) cudaFreeHost(c->fg_y_host);
-    c->fg_V = c->fg_Z = c->fg_w = c->fg_h = c->fg_y = nullptr;
+    c->fg_V = c->fg_Z = c->fg_w = nullptr;
+    c->fg_h = c->fg_y = nullptr;
     c->fg_h_host = c->fg_y_host = nullptr;
 }
 
