@@ -318,6 +318,10 @@ void free_net_ctx(gs_ctx* c);
 gs_status lp_rr_apply_f32(gs_ctx* c, const Plan* p, const void* x, void* y);
 size_t net_tc_weight_elems();
 size_t net_phi_weight_elems();
+size_t net_l1_weight_elems();
+gs_status net_l1_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw);
+gs_status net_l1_tc(gs_ctx* c, const float2* in, __nv_bfloat162* out, const __nv_bfloat16* Bw, const float2* U32,
+                    const int2* nbr, int64_t V, int* err);
 gs_status net_phi_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw);
 gs_status net_phi_tc(gs_ctx* c, const float2* in, float2* phi, const __nv_bfloat16* Bw, int64_t V, int* err);
 gs_status net_tc_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw);

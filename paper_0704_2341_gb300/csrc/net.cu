@@ -50,6 +50,7 @@ struct gs_net {
     float* host_red = nullptr;
     __nv_bfloat16* Btc = nullptr;   // C -> C weights packed for the tensor cores (C = 24)
     __nv_bfloat16* Bphi = nullptr;  // C -> 1 weights packed for the tensor cores (C = 24)
+    __nv_bfloat16* Bl1 = nullptr;   // 1 -> C weights packed for the tensor cores (C = 24)
     bool tc_dirty = true;           // Btc out of date with W[1]
     int* tc_err = nullptr;          // mapped host word raised by the tensor-core kernel
     int* tc_err_dev = nullptr;
@@ -145,11 +146,8 @@ __device__ __forceinline__ void stage_tile(const float2* __restrict__ in, const 
 }
 
 // out[V][R4][3] = sum_d W_d T_d ; threads: one per output row (>= 32)
-__device__ __forceinline__ void store_act(float2* p, float2 v) { *p = v; }
-__device__ __forceinline__ void store_act(__nv_bfloat162* p, float2 v) { *p = __floats2bfloat162_rn(v.x, v.y); }
-
-template <int CIN, int COUT, class WT, class OT = float2>
-__global__ void k_net_conv(const float2* __restrict__ in, OT* __restrict__ out, const WT* __restrict__ W,
+template <int CIN, int COUT, class WT>
+__global__ void k_net_conv(const float2* __restrict__ in, float2* __restrict__ out, const WT* __restrict__ W,
                            const float2* __restrict__ U32, const int2* __restrict__ nbr, int64_t V) {
     constexpr int K = 4 * CIN, R4 = 4 * COUT;
     __shared__ float2 T[K][kNCol];
@@ -176,10 +174,10 @@ __global__ void k_net_conv(const float2* __restrict__ in, OT* __restrict__ out, 
             for (int s = 0; s < kTS; ++s) {
                 const int64_t x = base + s;
                 if (x < V) {
-                    OT* dst = out + (x * R4 + R) * 3;
-                    store_act(dst + 0, acc[s * 3 + 0]);
-                    store_act(dst + 1, acc[s * 3 + 1]);
-                    store_act(dst + 2, acc[s * 3 + 2]);
+                    float2* dst = out + (x * R4 + R) * 3;
+                    dst[0] = acc[s * 3 + 0];
+                    dst[1] = acc[s * 3 + 1];
+                    dst[2] = acc[s * 3 + 2];
                 }
             }
         }
@@ -661,21 +659,23 @@ static gs_status net_forward(gs_ctx* c, gs_net* nt, bool bf16) {
         int cin, cout;
         layer_dims(nt->C, l, &cin, &cout);
         const bool tc = bf16 && nt->Btc && c->opt_net_kernel == 0;
+        if (tc && nt->tc_dirty) {
+            gs_status s;
+            if ((s = net_l1_pack(c, nt->W[0], nt->Bl1)) != GS_OK) return s;
+            if ((s = net_tc_pack(c, nt->W[1], nt->Btc)) != GS_OK) return s;
+            if ((s = net_phi_pack(c, nt->W[2], nt->Bphi)) != GS_OK) return s;
+            nt->tc_dirty = false;
+        }
         if (tc && l == 0) {
-            // the input of the tensor-core layer is kept in BF16 (in act[1]'s memory)
-            k_net_conv<1, 24, __nv_bfloat162, __nv_bfloat162><<<blocks, 96, 0, c->stream>>>(
-                nt->act[0], (__nv_bfloat162*)nt->act[1], nt->Wb[0], nt->U32, id->nbr, V);
-            c->launches++;
-            GS_CHECK_LAUNCH(c);
+            // 1 -> C on the tensor cores; its BF16 output (the C -> C layer's
+            // input) is kept in act[1]'s memory
+            gs_status s = net_l1_tc(c, nt->act[0], (__nv_bfloat162*)nt->act[1], nt->Bl1, nt->U32, id->nbr, V,
+                                    nt->tc_err_dev);
+            if (s != GS_OK) return s;
             continue;
         }
         if (tc && l == 1) {
             gs_status s;
-            if (nt->tc_dirty) {
-                if ((s = net_tc_pack(c, nt->W[1], nt->Btc)) != GS_OK) return s;
-                if ((s = net_phi_pack(c, nt->W[2], nt->Bphi)) != GS_OK) return s;
-                nt->tc_dirty = false;
-            }
             if ((s = net_conv_tc(c, (const __nv_bfloat162*)nt->act[1], nt->act[2], nt->Btc, nt->U32, id->nbr, V,
                                  nt->tc_err_dev)) != GS_OK)
                 return s;
@@ -946,7 +946,8 @@ gs_status gs_net_create(gs_net** out, int channels) {
     if (ok) *nt->tc_err = 0;
     if (ok && channels == 24)
         ok = cudaMalloc(&nt->Btc, net_tc_weight_elems() * sizeof(__nv_bfloat16)) == cudaSuccess &&
-             cudaMalloc(&nt->Bphi, net_phi_weight_elems() * sizeof(__nv_bfloat16)) == cudaSuccess;
+             cudaMalloc(&nt->Bphi, net_phi_weight_elems() * sizeof(__nv_bfloat16)) == cudaSuccess &&
+             cudaMalloc(&nt->Bl1, net_l1_weight_elems() * sizeof(__nv_bfloat16)) == cudaSuccess;
     if (ok) ok = cudaMemset(nt->counter, 0, sizeof(unsigned int)) == cudaSuccess &&
                  cudaDeviceSynchronize() == cudaSuccess;
     if (!ok) {
@@ -979,6 +980,7 @@ gs_status gs_net_destroy(gs_net* nt) {
     if (nt->tc_err) cudaFreeHost(nt->tc_err);
     cudaFree(nt->Btc);
     cudaFree(nt->Bphi);
+    cudaFree(nt->Bl1);
     cudaGetLastError();
     delete nt;
     return GS_OK;

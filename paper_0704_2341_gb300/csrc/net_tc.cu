@@ -537,6 +537,223 @@ __global__ void k_net_phi_pack(const float2* __restrict__ WT, __nv_bfloat16* __r
     }
 }
 
+// ---------------------------------------------------------------------------
+// The 1 -> C layer on the tensor cores: rows p = 3 x + a, K = 9 transports x
+// 4 spins x (re, im) = 72 (padded to 80, the padding columns of A zero once),
+// N = 192 (96 outputs x (re, im)); the threads stage U_d(x) in(x + d) for the
+// 4 input rows (FP32 links and activations through L1); BF16 output in the
+// layout the C -> C layer reads ([V][96][3] bf16x2).  128 rows per tile,
+// weights resident (30 KB), 192 TMEM columns, two CTAs per SM.
+// ---------------------------------------------------------------------------
+constexpr int kL1Rows = 128;
+constexpr int kL1K = 80;
+constexpr uint32_t kL1SBO = (kL1K / 8) * 128;          // 1280
+constexpr uint32_t kL1ABytes = kL1Rows * kL1K * 2;     // 20480
+constexpr uint32_t kL1BBytes = kN * kL1K * 2;          // 30720
+constexpr size_t kL1Smem = kL1ABytes + kL1BBytes + 128;
+constexpr int kL1Threads = 256;
+constexpr uint32_t kL1Idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                              ((uint32_t)(kL1Rows >> 4) << 24);
+
+__device__ __forceinline__ uint32_t l1_off(int r, int k) {
+    return (uint32_t)((r >> 3) * kL1SBO + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+__device__ __forceinline__ uint64_t l1_desc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)(kL1SBO >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+__global__ void __launch_bounds__(kL1Threads, 2)
+    k_net_l1_tc(const float2* __restrict__ in, __nv_bfloat162* __restrict__ out, const __nv_bfloat16* __restrict__ Bw,
+                const float2* __restrict__ U32, const int2* __restrict__ nbr, int64_t V, int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    unsigned char* sA = base;
+    unsigned char* sB = base + kL1ABytes;
+    __shared__ __align__(8) uint64_t bfull, mdone;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bfull)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mdone)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(su32(&tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // the padding columns 72..79 of A stay zero
+    for (int r = tid; r < kL1Rows; r += kL1Threads) {
+        *(uint4*)(sA + l1_off(r, 72)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tslot;
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bfull)), "r"(kL1BBytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         su32(sB)),
+                     "l"(Bw), "r"(kL1BBytes), "r"(su32(&bfull))
+                     : "memory");
+    }
+    const int64_t rows = 3 * V;
+    const int64_t ntiles = (rows + kL1Rows - 1) / kL1Rows;
+    int bad = 0;
+    uint32_t used = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t row0 = tile * kL1Rows;
+        const int64_t x0 = row0 / 3;
+        int64_t xl = (row0 + kL1Rows - 1) / 3;
+        if (xl > V - 1) xl = V - 1;
+        const int nsite = (int)(xl - x0 + 1);
+        const int off = (int)(row0 - 3 * x0);
+        // A: item = (site, transport): 4 input rows x 3 colours
+        for (int e = tid; e < nsite * 9; e += kL1Threads) {
+            const int sl = e / 9, d = e - sl * 9;
+            const int64_t x = x0 + sl;
+            int64_t y = x;
+            const float2* uu = nullptr;
+            bool dag = false;
+            if (d >= 1 && d <= 4) {
+                y = __ldg(&nbr[x * 4 + d - 1].x);
+                uu = U32 + (x * 4 + d - 1) * 9;
+            } else if (d >= 5) {
+                y = __ldg(&nbr[x * 4 + d - 5].y);
+                uu = U32 + (y * 4 + d - 5) * 9;
+                dag = true;
+            }
+            float2 u[9];
+            if (uu) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) u[i] = __ldg(uu + i);
+            }
+            const float2* src = in + y * 12;
+            const int r0 = 3 * sl - off;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 p0 = __ldg(src + 3 * k), p1 = __ldg(src + 3 * k + 1), p2 = __ldg(src + 3 * k + 2);
+                float2 t[3];
+                if (!uu) {
+                    t[0] = p0;
+                    t[1] = p1;
+                    t[2] = p2;
+                } else if (!dag) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float2 q0 = cmul(u[3 * a], p0), q1 = cmul(u[3 * a + 1], p1), q2 = cmul(u[3 * a + 2], p2);
+                        t[a] = make_float2(q0.x + q1.x + q2.x, q0.y + q1.y + q2.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float2 q0 = cmulc(u[a], p0), q1 = cmulc(u[3 + a], p1), q2 = cmulc(u[6 + a], p2);
+                        t[a] = make_float2(q0.x + q1.x + q2.x, q0.y + q1.y + q2.y);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int r = r0 + a;
+                    if (r >= 0 && r < kL1Rows)
+                        *(__nv_bfloat162*)(sA + l1_off(r, 2 * (4 * d + k))) = __floats2bfloat162_rn(t[a].x, t[a].y);
+                }
+            }
+        }
+        // rows past the last site (the last tile only) are zero
+        for (int e = tid; e < kL1Rows * 36; e += kL1Threads) {
+            const int r = e / 36, q = e - r * 36;
+            if (row0 + r >= rows) *(__nv_bfloat162*)(sA + l1_off(r, 2 * q)) = __floats2bfloat162_rn(0.f, 0.f);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            if (used == 0 && !mbar_wait(su32(&bfull), 0u)) {
+                bad = 1;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+                for (int ks = 0; ks < kL1K / 16; ++ks) {
+                    const uint64_t ad = l1_desc(su32(sA) + ks * 256);
+                    const uint64_t bd = l1_desc(su32(sB) + ks * 256);
+                    const uint32_t acc = ks > 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(kL1Idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&mdone))
+                             : "memory");
+            }
+        }
+        if (__syncthreads_or(bad)) {
+            bad = 1;
+            break;
+        }
+        ++used;
+        if (!mbar_wait(su32(&mdone), (used - 1) & 1u)) bad = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!__syncthreads_or(bad)) {
+            // warp w: lanes 32 (w % 4) .. + 31, columns 96 (w / 4) .. + 95
+            const int wq = warp & 3, ch = warp >> 2;
+            const int r = 32 * wq + lane;
+            const int64_t p = row0 + r;
+            const int64_t x = p / 3;
+            const int a = (int)(p - 3 * x);
+            for (int c = 96 * ch; c < 96 * ch + 96; c += 32) {
+                uint32_t v[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                      "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                      "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (p < rows) {
+                    __nv_bfloat162* dst = out + (x * kRC + c / 2) * 3 + a;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        dst[3 * i] = __floats2bfloat162_rn(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                }
+            }
+        } else {
+            bad = 1;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        if (__syncthreads_or(bad)) {
+            bad = 1;
+            break;
+        }
+    }
+    if (bad && tid == 0) atomicExch(err, 1);
+    if (tid == 0 && used == 0) mbar_wait(su32(&bfull), 0u);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+}
+
+// B of the 1 -> C layer from its FP32 master weights WT[d][k][R] (k < 4)
+__global__ void k_net_l1_pack(const float2* __restrict__ WT, __nv_bfloat16* __restrict__ Bw) {
+    const int n = kN * kL1K;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int np = e / kL1K, kp = e - np * kL1K;
+        float v = 0.f;
+        if (kp < 72) {
+            const int o = np >> 1, cout = np & 1, q = kp >> 1, cin = kp & 1;
+            const int d = q >> 2, k = q & 3;
+            const float2 w = WT[((int64_t)d * 4 + k) * kRC + o];
+            v = cout == 0 ? (cin == 0 ? w.x : -w.y) : (cin == 0 ? w.y : w.x);
+        }
+        Bw[l1_off(np, kp) / 2] = __float2bfloat16_rn(v);
+    }
+}
+
 }  // namespace
 
 size_t net_tc_weight_elems() { return (size_t)kChunks * kN * kKC; }
@@ -549,6 +766,26 @@ gs_status net_tc_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw) {
 }
 
 size_t net_phi_weight_elems() { return (size_t)kPhiN * kPhiK; }
+size_t net_l1_weight_elems() { return (size_t)kN * kL1K; }
+
+gs_status net_l1_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw) {
+    k_net_l1_pack<<<grid_for(kN * kL1K, 256, 64), 256, 0, c->stream>>>(WT, Bw);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+gs_status net_l1_tc(gs_ctx* c, const float2* in, __nv_bfloat162* out, const __nv_bfloat16* Bw, const float2* U32,
+                    const int2* nbr, int64_t V, int* err) {
+    GS_CUDA(c, cudaFuncSetAttribute(k_net_l1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kL1Smem));
+    const int64_t ntiles = (3 * V + kL1Rows - 1) / kL1Rows;
+    const int64_t cap = 2LL * c->num_sms;
+    const int grid = (int)(ntiles < cap ? ntiles : cap);
+    k_net_l1_tc<<<grid, kL1Threads, kL1Smem, c->stream>>>(in, out, Bw, U32, nbr, V, err);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
 
 gs_status net_phi_pack(gs_ctx* c, const float2* WT, __nv_bfloat16* Bw) {
     k_net_phi_pack<<<grid_for(kPhiN * kPhiK, 256, 64), 256, 0, c->stream>>>(WT, Bw);
