@@ -213,17 +213,17 @@ __global__ void k_bicg_p(const double2* __restrict__ r, const double2* __restric
 // generic BLAS-1
 // ---------------------------------------------------------------------------
 
-// out[k] (+)= <X_k, y> = sum conj(X_k) y, k < nvec.  grid = (gx, ceil(nvec / 8)).
+// out[k] (+)= <X_k, y> = sum conj(X_k) y, k < nvec.  grid = (gx, ceil(nvec / chunk)).
 __global__ void k_multidot(const double2* __restrict__ X, int64_t ld, const double2* __restrict__ y,
-                           int64_t n, int nvec, double2* out, int accumulate, double* partial,
+                           int64_t n, int nvec, int chunk, double2* out, int accumulate, double* partial,
                            unsigned int* counter) {
-    // block (bx, chunk): the dots of vectors 8 chunk .. 8 chunk + 7 with y over
-    // the block's strided range (y read once for eight vectors); the last
-    // block adds the per-block partials of every vector in block order
+    // block (bx, c): the dots of vectors chunk c .. chunk c + chunk - 1 (chunk
+    // <= 8) with y over the block's strided range (y read once for them); the
+    // last block adds the per-block partials of every vector in block order
     __shared__ double sm[kBlas / 32][2 * kDotChunk];
     __shared__ bool am_last;
-    const int k0 = blockIdx.y * kDotChunk;
-    const int nk = nvec - k0 < kDotChunk ? nvec - k0 : kDotChunk;
+    const int k0 = blockIdx.y * chunk;
+    const int nk = nvec - k0 < chunk ? nvec - k0 : chunk;
     double a[2 * kDotChunk];
 #pragma unroll
     for (int q = 0; q < 2 * kDotChunk; ++q) a[q] = 0.0;
@@ -242,10 +242,12 @@ __global__ void k_multidot(const double2* __restrict__ X, int64_t ld, const doub
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < 2 * kDotChunk; ++q) {
-        double v = a[q];
+        if (q < 2 * nk) {  // block-uniform
+            double v = a[q];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) sm[warp][q] = v;
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) sm[warp][q] = v;
+        }
     }
     __syncthreads();
     const unsigned nblocks = gridDim.x * gridDim.y;
@@ -380,13 +382,16 @@ gs_status launch_multidot(gs_ctx* c, RedScratch red, const double2* X, int64_t l
     if (nvec <= 0) return GS_OK;
     // enough blocks in flight to stream long vectors at HBM bandwidth, within
     // the partial scratch (nvec x gx complex)
-    const int nchunks = (nvec + kDotChunk - 1) / kDotChunk;
+    // long vectors: eight vectors per block against one load of y; short
+    // ones: one vector per block (more blocks, short reduction tails)
+    const int chunk = n >= 65536 ? kDotChunk : 1;
+    const int nchunks = (nvec + chunk - 1) / chunk;
     int64_t cap = (int64_t)c->num_sms * 8 / nchunks;
     if (cap < 64) cap = 64;
     if (cap > kRedScratchDoubles / (2 * nvec)) cap = kRedScratchDoubles / (2 * nvec);
     const int gx = grid_for(n, kBlas, (int)cap);
     dim3 g(gx, nchunks);
-    k_multidot<<<g, kBlas, 0, c->stream>>>(X, ld, y, n, nvec, dev_out, accumulate, red.partial,
+    k_multidot<<<g, kBlas, 0, c->stream>>>(X, ld, y, n, nvec, chunk, dev_out, accumulate, red.partial,
                                            red.counter);
     c->launches++;
     GS_CHECK_LAUNCH(c);
