@@ -95,7 +95,10 @@ typedef struct {
     double relax_cap;      /* largest relaxed inner tolerance [1e-4] */
     int    inner_solver;   /* low-precision stage of the mixed inner solve: GS_INNER_BICGSTAB,
                             * or GS_INNER_FGMRES_NET = flexible GMRES(inner_restart) with the
-                            * network attached by gs_set_net as right preconditioner
+                            * network attached by gs_set_net as right preconditioner, run in
+                            * FP32 (basis vectors, D_rr stencil, products; dot-product sums
+                            * in FP64); each pass reduces the residual by lowp_tol and the
+                            * FP64 true residual is recomputed after it
                             * [GS_INNER_BICGSTAB] */
     int    inner_restart;  /* Krylov steps of one FGMRES-with-network pass, 1..64 [16] */
 } gs_solve_opts;
@@ -143,10 +146,11 @@ enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 
  * cooperative kernel (grid barriers with bounded waits between its phases;
  * the default), 1 = five kernel launches per iteration with the convergence
  * flag read back while iterations are queued.
- * GS_OPT_NET_KERNEL: 0 = the C -> C layer of a 24-channel network runs on the
- * tensor cores (tcgen05.mma, BF16 operands: the transported activations are
- * rounded to BF16 as well as the weights; FP32 accumulation; the default),
- * 1 = every layer on the CUDA cores (FP32 activations, BF16 weights). */
+ * GS_OPT_NET_KERNEL: 0 = the contractions of a 24-channel network (1 -> C,
+ * C -> C, and the weights-first half of C -> 1) run on the tensor cores
+ * (tcgen05.mma, BF16 operands: the transported activations are rounded to
+ * BF16 as well as the weights; FP32 accumulation; the default), 1 = every
+ * layer on the CUDA cores (FP32 activations, BF16 weights). */
 gs_status gs_set_option(gs_ctx* ctx, int option, int value);
 gs_status gs_get_option(gs_ctx* ctx, int option, int* value);
 
@@ -333,9 +337,13 @@ gs_status gs_solve_rr(gs_ctx* ctx, int type, int dir, int inverse, const void* t
  * output is read on the rest set.  The paper has no learned component; its
  * own preconditioner is a hand-made approximation of the Schur complement
  * (Section 3, Section 4): this one is fitted to pairs (t, D_rr^-1 t) that
- * gs_solve_rr produces.  FP32 arithmetic; FP32 master weights for training,
- * BF16 weights for inference.  A network is not tied to a context: it uses
- * the links of the context it is called with. */
+ * gs_solve_rr produces (or t = D_rr z for a given z).  Training: FP32
+ * arithmetic and FP32 master weights.  Inference: BF16 weights; with C = 24
+ * and GS_OPT_NET_KERNEL = 0 the contractions of all three layers run on the
+ * tensor cores (tcgen05.mma, BF16 operands including the transported
+ * activations, FP32 accumulation), otherwise on the CUDA cores with FP32
+ * activations.  A network is not tied to a context: it uses the links of the
+ * context it is called with. */
 typedef struct gs_net gs_net;
 gs_status gs_net_create(gs_net** net_out, int channels);
 gs_status gs_net_destroy(gs_net* net);
@@ -346,8 +354,9 @@ gs_status gs_net_set_weights(gs_net* net, int layer, const void* w_host);
  * step; same layout as gs_net_set_weights (host memory). */
 gs_status gs_net_get(gs_net* net, int what, int layer, void* host_out);
 /* y = M t on the rest set; t_dev, y_dev complex128 [n_r][4][3] (label order).
- * BF16 weights; the C -> C layer as GS_OPT_NET_KERNEL selects.  Synchronises
- * the stream; GS_TIMEOUT if the tensor-core layer gave up on a wait. */
+ * BF16 weights; kernels as GS_OPT_NET_KERNEL selects.  Synchronises the
+ * stream; GS_TIMEOUT if a tensor-core kernel gave up on a wait (each wait is
+ * bounded by one second). */
 gs_status gs_net_apply(gs_ctx* ctx, gs_net* net, int type, int dir, int inverse,
                        const void* t_dev, void* y_dev);
 /* One training step on `batch` pairs: t_dev, z_dev complex64 [batch][n_r][4][3]
