@@ -269,3 +269,30 @@ def test_relaxed_inner_tolerance_same_solution_fewer_iterations(env, prec):
     assert rel(xs[1], xs[0]) <= 1e-7
     assert its[1] < its[0]
     ctx.close()
+
+
+def test_profile_phases_of_the_persistent_solver(env):
+    """gs_profile_phases: while profiling, block 0 of the persistent FP64
+    BiCGStab counts cycles per phase; the counts are non-negative, the two
+    stencil phases are the largest work phases, and they are cleared when
+    profiling restarts."""
+    torch, gs = env
+    dims = (8, 8, 4, 4)
+    U = li.random_gauge(dims, 0.3, 5)
+    ctx = gs.Context(dims, 0.1, torch.cuda.current_stream().cuda_stream)
+    ctx.set_gauge(to_dev(U, torch))
+    f = to_dev(li.gaussian_source(dims, 7), torch)
+    x = torch.empty_like(f)
+    ctx.schur_solve(1, 0, 0, f, x)
+    ctx.profile(True)
+    ctx.schur_solve(1, 0, 0, f, x)
+    ph = ctx.profile_phases()
+    ctx.profile(False)
+    assert len(ph) == 15 and all(v >= 0 for v in ph)
+    assert ph[0] > 0 and ph[6] > 0                  # v = D p and t = D s
+    work = [ph[3 * s] for s in range(5)]
+    assert max(work) in (ph[0], ph[6])
+    ctx.profile(True)
+    assert sum(ctx.profile_phases()) == 0.0
+    ctx.profile(False)
+    ctx.close()
