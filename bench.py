@@ -10,7 +10,12 @@ residual ||f - D x|| / ||f||.  Field: SU(3) plaquette action at beta = 5.4
 one complex Gaussian source (seed 100).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle instead (see the design doc for its sample).
+oracle instead: each timed step is one complete P_I solve of the same
+workload, each warm-up step one S_bb apply.  Further sections of the line:
+mixed-precision and learned (network + FGMRES) inner solves on the same
+workload, the low-precision stencil on 32^3 x 64, one source of the
+32^3 x 64 learned-preconditioner workload, and (``--batched``) several
+sources and lattices solved together.
 """
 from __future__ import annotations
 
@@ -91,7 +96,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%s.csv" % index)
+        import tempfile
+        self.path = os.path.join(os.environ.get("GSCHUR_CLOCK_LOG_DIR", tempfile.gettempdir()),
+                                 "gschur_clocks_rank%s.csv" % index)
 
     def start(self):
         try:

@@ -8,7 +8,7 @@
 // result meets the same FP64 tolerance as the plain solve; the low-precision
 // solve only has to reduce the residual by a few digits per cycle.  If a
 // cycle stops making progress, the remaining correction is computed by the
-// plain FP64 BiCGStab (the fallback and the judge of the result).
+// plain FP64 BiCGStab (the fallback, and the arbiter of the result).
 //
 // Low-precision layouts (compact rest-set index k = label - n_b):
 //   spinors: SoA of 16-byte vectors, component-major: FP32 -> 6 float4 per
