@@ -100,3 +100,15 @@ def test_rejects_odd_extent():
     with pytest.raises(ValueError):
         permute.permutation((3, 4, 4, 4), TYPE_II, 0)
     permute.permutation((3, 4, 4, 4), TYPE_II, 1)
+
+
+def test_inverse_type_I_coarse_set_4x4x4x4_hand_derived():
+    """P_I^T on 4^4 (s = x0 + 4 x1 + 16 x2 + 64 x3): the coarse set is
+    {q(0), ..., q(15)}, the labels of sites 0..15 (x2 = x3 = 0).  Of these the
+    all-even sites 0, 2, 8, 10 are the first four coarse sites of P_I (labels
+    0..3); the other twelve are the first twelve rest sites (labels 16..27).
+    As sites: x0 = 0..3 with x1 = x2 = 0, and x0 = 0..3, x1 = 0..2, x2 = 1."""
+    q, nb = permute.permutation((4, 4, 4, 4), TYPE_I, 0, True)
+    assert nb == 16
+    assert list(q[:16]) == [0, 16, 1, 17, 18, 19, 20, 21, 2, 22, 3, 23, 24, 25, 26, 27]
+    assert sorted(q[:16]) == list(range(4)) + list(range(16, 28))
