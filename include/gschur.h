@@ -141,7 +141,7 @@ gs_status gs_set_gauge(gs_ctx* ctx, const void* U_dev);
  * direction (four partial sums combined in shared memory).  gs_get_option
  * returns the forced value, or under autotuning the variant chosen most
  * recently. */
-enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 3 };
+enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 3, GS_OPT_MULTI_BATCH = 4 };
 /* GS_OPT_INNER_KERNEL: 0 = each inner BiCGStab solve runs as one persistent
  * cooperative kernel (grid barriers with bounded waits between its phases;
  * the default), 1 = five kernel launches per iteration with the convergence
@@ -150,7 +150,12 @@ enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 
  * C -> C, and the weights-first half of C -> 1) run on the tensor cores
  * (tcgen05.mma, BF16 operands: the transported activations are rounded to
  * BF16 as well as the weights; FP32 accumulation; the default), 1 = every
- * layer on the CUDA cores (FP32 activations, BF16 weights). */
+ * layer on the CUDA cores (FP32 activations, BF16 weights).
+ * GS_OPT_MULTI_BATCH: how schur_solve_multi (and schur_solve_batched per
+ * problem) shapes its work: 0 = the sources of a problem share every launch
+ * when the rest set has at most 16384 sites, where one source leaves the GPU
+ * latency bound, else they are solved one at a time by the single-source
+ * solver (the default); 1 = always together; 2 = always one at a time. */
 gs_status gs_set_option(gs_ctx* ctx, int option, int value);
 gs_status gs_get_option(gs_ctx* ctx, int option, int* value);
 
@@ -290,7 +295,10 @@ gs_status wilson_apply_lowp(gs_ctx* ctx, int type, int dir, int inverse, int pre
  * application per Arnoldi step).  f_dev, x_dev: complex128
  * [nrhs][V][4][3], site order.  stats (may be NULL) aggregates: iterations
  * summed, true_residual and outer_residual the worst over the sources.
- * Synchronises the stream. */
+ * Whether the sources actually share launches is set by GS_OPT_MULTI_BATCH
+ * (by default only on rest sets of at most 16384 sites; larger problems are
+ * solved one source at a time with the same options and results to the same
+ * tolerance).  Synchronises the stream. */
 gs_status schur_solve_multi(gs_ctx* ctx, int type, int dir, int inverse, int nrhs,
                             const void* f_dev, void* x_dev, const gs_solve_opts* opts,
                             gs_solve_stats* stats);

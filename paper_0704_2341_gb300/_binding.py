@@ -22,7 +22,7 @@ GS_TYPE_I, GS_TYPE_II = 1, 2
 GS_F64, GS_F32, GS_BF16 = 0, 1, 2
 GS_GMRES, GS_BICGSTAB = 0, 1
 GS_INNER_BICGSTAB, GS_INNER_FGMRES_NET = 0, 1
-GS_OPT_STENCIL_VARIANT, GS_OPT_INNER_KERNEL, GS_OPT_NET_KERNEL = 1, 2, 3
+GS_OPT_STENCIL_VARIANT, GS_OPT_INNER_KERNEL, GS_OPT_NET_KERNEL, GS_OPT_MULTI_BATCH = 1, 2, 3, 4
 GS_PROF_STENCIL_F64, GS_PROF_STENCIL_F32, GS_PROF_STENCIL_BF16, GS_PROF_SOLVER_F64, \
     GS_PROF_SOLVER_LP = range(5)
 

@@ -196,6 +196,11 @@ gs_status gs_set_option(gs_ctx* c, int option, int value) {
         c->opt_net_kernel = value;
         return GS_OK;
     }
+    if (option == GS_OPT_MULTI_BATCH) {
+        if (value < 0 || value > 2) return set_err(c, GS_EINVAL, "multi-source batching %d not in 0..2", value);
+        c->opt_multi_batch = value;
+        return GS_OK;
+    }
     return set_err(c, GS_EINVAL, "unknown option %d", option);
 }
 
@@ -211,6 +216,10 @@ gs_status gs_get_option(gs_ctx* c, int option, int* value) {
     }
     if (option == GS_OPT_NET_KERNEL) {
         *value = c->opt_net_kernel;
+        return GS_OK;
+    }
+    if (option == GS_OPT_MULTI_BATCH) {
+        *value = c->opt_multi_batch;
         return GS_OK;
     }
     return set_err(c, GS_EINVAL, "unknown option %d", option);

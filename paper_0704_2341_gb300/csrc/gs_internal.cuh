@@ -199,7 +199,8 @@ struct gs_ctx {
     void* mixed = nullptr;             // mixed-precision state (mixed.cu)
     int opt_stencil_variant = 0;       // 0 = autotune, 1/3/4 = site (4/6/8 blocks), 2 = direction
     int opt_inner_kernel = 0;          // 0 = persistent cooperative BiCGStab, 1 = one launch per phase
-    int opt_net_kernel = 0;            // 0 = tensor-core C -> C layer (C = 24), 1 = CUDA cores only
+    int opt_net_kernel = 0;            // 0 = tensor-core network kernels (C = 24), 1 = CUDA cores only
+    int opt_multi_batch = 0;           // 0 = by rest-set size, 1 = sources together, 2 = one at a time
     void* persist = nullptr;           // persistent-solver scratch (persistent.cu)
     void* multi = nullptr;             // multi-RHS workspaces (multi.cu)
     int coop_block_cap = 0;            // cap on cooperative grids (0 = whole GPU; batched solves)

@@ -138,3 +138,27 @@ def test_multi_rejects_bad_arguments(env):
     with pytest.raises(gs.GschurError):   # the multi-source solve runs low-precision inner solves
         ctx.schur_solve_multi(1, 0, 0, 1, z, z.clone(), gs.gs_default_opts(inner_prec=gs.GS_F64))
     ctx.close()
+
+
+def test_batch_shape_option_gives_the_same_solutions(env):
+    """GS_OPT_MULTI_BATCH: sources together (1) or one at a time (2) solve to
+    the same 1e-10 residual and agree to the solver tolerance; the default (0)
+    shares launches on this 8^4-like rest set and reports 0."""
+    torch, gs = env
+    dims = (8, 8, 4, 8)
+    U = li.random_gauge(dims, 0.3, 4)
+    ctx = _ctx(gs, torch, dims, -0.1, U)
+    assert ctx.get_option(gs.GS_OPT_MULTI_BATCH) == 0
+    f = to_dev(np.ascontiguousarray(li.gaussian_source(dims, 31, n_src=3)), torch)
+    o = gs.gs_default_opts(inner_prec=gs.GS_F32)
+    xs = []
+    for mode in (1, 2):
+        ctx.set_option(gs.GS_OPT_MULTI_BATCH, mode)
+        x = torch.zeros_like(f)
+        st = ctx.schur_solve_multi(1, 0, 0, 3, f, x, o)
+        assert st.true_residual <= 1e-10
+        xs.append(x.cpu().numpy())
+    assert rel(xs[0], xs[1]) <= 1e-8
+    with pytest.raises(gs.GschurError):
+        ctx.set_option(gs.GS_OPT_MULTI_BATCH, 3)
+    ctx.close()
