@@ -18,10 +18,12 @@ Everything here is complex128 and written for clarity, not speed:
                  (Section 1, the partition, Eq. for S_bb and the UL product);
 * ``krylov``  -- textbook BiCGStab (van der Vorst 1992) and restarted
                  GMRES(m) (Saad & Schultz 1986), the solvers the paper uses
-                 or the configuration asks for (Section 4).
+                 or the configuration asks for (Section 4);
+* ``reusken`` -- the second-order Schur-complement approximation of
+                 Section 3 (site-block diagonal d and row sums d~).
 
 Parity status of each function is listed in the module headers; every
 function listed is pinned by a ``-m "not gpu"`` test except where a module
 header says "parity unpinned".
 """
-from . import dirac, permute, schur, krylov, net  # noqa: F401
+from . import dirac, permute, schur, krylov, net, reusken  # noqa: F401
