@@ -326,6 +326,19 @@ gs_status gs_lowp_unpack_multi(gs_ctx* ctx, int type, int dir, int inverse, int 
 gs_status wilson_apply_lowp_multi(gs_ctx* ctx, int type, int dir, int inverse, int prec,
                                   int nrhs, const void* x_lp_dev, void* y_lp_dev);
 
+/* y_b = S~_bb x_b: the second-order Schur-complement approximation of
+ * Section 3 of the paper,
+ *   S~_bb = D_bb - D_br (d^-1 + d~^-1 - d^-1 D_rr d~^-1) D_rb,
+ * d the diagonal and d~ the row sums of D_rr, both read as 12 x 12 blocks per
+ * rest site (spin x colour).  No inner solve: three stencil launches and one
+ * 12 x 12 block product per rest site; the block inverses of d~ are built on
+ * the first call per permutation and gauge field (GS_NONFINITE if one is
+ * singular).  xb_dev, yb_dev: complex128 [n_b][4][3] in label order, as for
+ * schur_apply.  Uses the context's inner-solve workspace; asynchronous
+ * except for that first call. */
+gs_status schur_apply_reusken(gs_ctx* ctx, int type, int dir, int inverse, const void* xb_dev,
+                              void* yb_dev);
+
 /* z = D_rr^-1 t on the rest set of (type, dir, inverse): the inner solve of
  * S_bb on its own (opts->inner_tol, inner_prec, inner_solver as for
  * schur_solve).  t_dev, z_dev: complex128 [n_r][4][3] in label order (labels

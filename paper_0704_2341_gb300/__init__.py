@@ -21,4 +21,5 @@ __all__ = ["Context", "GschurError", "gs_create", "gs_destroy", "gs_set_gauge",
            "wilson_apply_lowp_multi", "gs_solve_rr", "Net", "gs_set_net", "GS_INNER_BICGSTAB",
            "GS_INNER_FGMRES_NET",
            "GS_TYPE_I", "GS_TYPE_II", "GS_F64", "GS_F32", "GS_BF16", "GS_GMRES",
-           "GS_BICGSTAB", "GS_OK", "GS_MAXITER", "GS_BREAKDOWN", "STATUS_NAMES"]
+           "GS_BICGSTAB", "GS_OK", "GS_MAXITER", "GS_BREAKDOWN", "STATUS_NAMES",
+           "schur_apply_reusken", "GS_OPT_MULTI_BATCH"]

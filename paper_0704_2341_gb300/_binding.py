@@ -34,7 +34,7 @@ EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson
            "gs_get_option", "schur_solve_multi", "schur_solve_batched", "gs_lowp_pack_multi",
            "gs_lowp_unpack_multi", "wilson_apply_lowp_multi", "gs_solve_rr", "gs_net_create",
            "gs_net_destroy", "gs_net_set_weights", "gs_net_get", "gs_net_apply",
-           "gs_net_train_step", "gs_set_net", "gs_profile_phases")
+           "gs_net_train_step", "gs_set_net", "gs_profile_phases", "schur_apply_reusken")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -106,6 +106,7 @@ def _load():
                                     ctypes.POINTER(ctypes.c_float)]),
         "gs_set_net": (i32, [vp, vp]),
         "gs_profile_phases": (i32, [vp, ctypes.POINTER(ctypes.c_double), i32]),
+        "schur_apply_reusken": (i32, [vp, i32, i32, i32, vp, vp]),
         "schur_solve_multi": (i32, [vp, i32, i32, i32, i32, vp, vp, ctypes.POINTER(gs_solve_opts),
                                     ctypes.POINTER(gs_solve_stats)]),
         "schur_solve_batched": (i32, [i32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
@@ -233,6 +234,10 @@ def wilson_apply_noalloc(dims, m0, U, x, y, stream=None):
 
 def gs_profile(ctx, enable):
     return _check(ctx, lib.gs_profile(ctx, int(bool(enable))))
+
+
+def schur_apply_reusken(ctx, ptype, dir, inverse, xb, yb):
+    return _check(ctx, lib.schur_apply_reusken(ctx, ptype, dir, int(bool(inverse)), _ptr(xb), _ptr(yb)))
 
 
 def gs_profile_phases(ctx):
@@ -451,6 +456,9 @@ class Context:
 
     def profile_phases(self):
         return gs_profile_phases(self.handle)
+
+    def schur_apply_reusken(self, ptype, dir, inverse, xb, yb):
+        return schur_apply_reusken(self.handle, ptype, dir, inverse, xb, yb)
 
     def solve_rr(self, ptype, dir, inverse, t, z, opts=None, allow=(GS_OK,)):
         return gs_solve_rr(self.handle, ptype, dir, inverse, t, z, opts, allow)

@@ -114,6 +114,8 @@ struct Plan {
     double2* links = nullptr;    // [V][4][9] -1/2 U_mu(perm[j]) in label order
     bool links_ready = false;
     long long hops[2][2] = {{0, 0}, {0, 0}};  // [out set][in set] in-set neighbour terms (0 = b, 1 = r)
+    double2* dtinv = nullptr;    // [V - nb][12][12] inverse block row sums of D_rr (Reusken), lazily
+    bool dtinv_ready = false;
 };
 
 // Event-timed stencil launches (gs_profile).

@@ -178,6 +178,7 @@ void free_plan(Plan* p) {
     cudaFree(p->label);
     cudaFree(p->nbr);
     cudaFree(p->links);
+    cudaFree(p->dtinv);
     delete p;
 }
 
@@ -189,6 +190,7 @@ gs_status pack_plan_links(gs_ctx* c, Plan* p) {
     c->launches++;
     GS_CHECK_LAUNCH(c);
     p->links_ready = true;
+    p->dtinv_ready = false;   // the Reusken block inverses depend on the links
     return GS_OK;
 }
 
