@@ -468,6 +468,44 @@ def batched_section(torch, gs, li, reps=2):
             "timing": "wall clock around the call (host threads per lattice), %d repetitions" % reps}
 
 
+def reusken_section(torch, gs, li, reps=20):
+    """The Section 3 approximation on the 8^4 workload (m0 = -0.4, the four
+    permutations): time of one S~_bb apply (no inner solve) against one exact
+    S_bb apply (inner BiCGStab to 1e-12), CUDA events, and the distance
+    ||S~ x - S x|| / ||S x|| on a Gaussian x_b."""
+    dims, U = li.workload_gauge(FIELD)
+    stream = torch.cuda.current_stream()
+    ctx = gs.Context(dims, M0, stream.cuda_stream)
+    ctx.set_gauge(torch.from_numpy(U).to("cuda"))
+    out = {"workload": WORKLOAD.split(", FP64")[0] + ", one Gaussian x_b per permutation", "permutations": {}}
+    opts = gs.gs_default_opts()
+    for (t, mu, inv) in PERMS:
+        perm = torch.empty(ctx.volume, dtype=torch.int32, device="cuda")
+        nb = ctx.get_permutation(t, mu, inv, perm)
+        rng = np.random.default_rng(5)
+        xb = torch.from_numpy(rng.standard_normal(nb * 12) + 1j * rng.standard_normal(nb * 12)).to("cuda")
+        ya, ys = torch.empty_like(xb), torch.empty_like(xb)
+        ctx.schur_apply_reusken(t, mu, inv, xb, ya)
+        ctx.schur_apply(t, mu, inv, xb, ys, opts)
+        times = {}
+        for name, call in (("reusken", lambda: ctx.schur_apply_reusken(t, mu, inv, xb, ya)),
+                           ("exact", lambda: ctx.schur_apply(t, mu, inv, xb, ys, opts))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                call()
+            b.record(stream)
+            b.synchronize()
+            times[name] = a.elapsed_time(b) / reps
+        key = ("P_%s%s" % ("I" if t == 1 else "II", "^T" if inv else ""))
+        out["permutations"][key] = {
+            "reusken_apply_ms": times["reusken"], "exact_apply_ms": times["exact"],
+            "speedup": times["exact"] / times["reusken"],
+            "rel_distance": float(torch.linalg.norm(ya - ys) / torch.linalg.norm(ys))}
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -481,7 +519,7 @@ def main():
                     help="skip the learned-preconditioner sections")
     ap.add_argument("--batched", action="store_true",
                     help="add the batched multi-lattice multi-source section (about 6 minutes)")
-    ap.add_argument("--only", default=None, choices=["batched", "learned_large"],
+    ap.add_argument("--only", default=None, choices=["batched", "learned_large", "reusken"],
                     help="run one section alone and print it")
     ap.add_argument("--_cpu-sample", action="store_true", dest="cpu_sample")
     ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp"],
@@ -504,7 +542,8 @@ def main():
         g.build()
         import paper_0704_2341_gb300 as gs
         import lattice_inputs as li
-        out = batched_section(torch, gs, li) if args.only == "batched" else learned_large(torch, gs, li)
+        out = {"batched": batched_section, "learned_large": learned_large,
+               "reusken": reusken_section}[args.only](torch, gs, li)
         print(json.dumps(out), flush=True)
         return
 
