@@ -20,10 +20,12 @@ Everything here is complex128 and written for clarity, not speed:
                  GMRES(m) (Saad & Schultz 1986), the solvers the paper uses
                  or the configuration asks for (Section 4);
 * ``reusken`` -- the second-order Schur-complement approximation of
-                 Section 3 (site-block diagonal d and row sums d~).
+                 Section 3 (site-block diagonal d and row sums d~);
+* ``vcycle``  -- the cyclic-reduction V-cycle preconditioner of Section 4
+                 built from it, and BiCGStab preconditioned by it (R).
 
 Parity status of each function is listed in the module headers; every
 function listed is pinned by a ``-m "not gpu"`` test except where a module
 header says "parity unpinned".
 """
-from . import dirac, permute, schur, krylov, net, reusken  # noqa: F401
+from . import dirac, permute, schur, krylov, net, reusken, vcycle  # noqa: F401

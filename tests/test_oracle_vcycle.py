@@ -1,0 +1,48 @@
+"""The V-cycle preconditioner of Section 4 (oracle): exact with exact Schur
+complements (block UL factorisation), and a strong preconditioner with the
+Section 3 approximation."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as sla
+
+import lattice_inputs as li
+from oracle import dirac, krylov, permute, vcycle
+
+I, II = permute.TYPE_I, permute.TYPE_II
+
+
+@pytest.mark.parametrize("levels", [[(I, 0, False), (I, 0, False)], [(II, 0, False), (II, 1, False)],
+                                    [(I, 0, True), (I, 0, True)], [(II, 0, True), (II, 3, True)]])
+def test_exact_schur_vcycle_is_the_inverse(levels):
+    """Three levels with exact Schur complements and exact inner solves: one
+    V-cycle is D^-1 (the block UL factorisation applied level by level)."""
+    dims = (4, 4, 4, 4)
+    U = li.random_gauge(dims, 0.3, 0)
+    D = dirac.wilson_matrix(U, dims, 0.1).tocsr()
+    f = li.gaussian_source(dims, 100).ravel()
+    x = vcycle.VCycle(D, dims, levels, schur="exact").apply(f)
+    xs = sla.spsolve(D.tocsc(), f)
+    assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+
+
+def test_coarse_dims():
+    assert vcycle.coarse_dims((8, 8, 4, 4), I) == (4, 4, 2, 2)
+    assert vcycle.coarse_dims((8, 8, 4, 4), II, 2) == (8, 8, 2, 4)
+
+
+def test_reusken_vcycle_preconditions_bicgstab():
+    """With the Section 3 approximation at both coarse levels (exact inner
+    solves), right-preconditioned BiCGStab reaches 1e-8 in a handful of steps
+    and its average convergence rate R drops far below the plain one
+    (measured here: 6 steps, R = 0.04, against 56 steps, R = 0.72)."""
+    dims = (8, 8, 4, 4)
+    U = li.random_gauge(dims, 0.3, 1)
+    D = dirac.wilson_matrix(U, dims, -0.2).tocsr()
+    f = li.gaussian_source(dims, 100).ravel()
+    _, plain = krylov.bicgstab(lambda v: D @ v, f, tol=1e-8, maxiter=5000)
+    vc = vcycle.VCycle(D, dims, [(II, 0, True), (II, 1, True)], schur="reusken")
+    x, info = vcycle.preconditioned_bicgstab(D, f, vc, tol=1e-8, maxiter=100)
+    assert info["converged"]
+    assert np.linalg.norm(D @ x - f) <= 1e-7 * np.linalg.norm(f)
+    assert info["iters"] <= 10 < plain["iters"]
+    assert info["R"] < 0.2 < krylov.convergence_rate(plain["history"])
