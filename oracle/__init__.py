@@ -22,7 +22,8 @@ Everything here is complex128 and written for clarity, not speed:
 * ``reusken`` -- the second-order Schur-complement approximation of
                  Section 3 (site-block diagonal d and row sums d~);
 * ``vcycle``  -- the cyclic-reduction V-cycle preconditioner of Section 4
-                 built from it, and BiCGStab preconditioned by it (R).
+                 built from it, and BiCGStab preconditioned by it (R);
+* ``spectra`` -- dense spectra of S, S~ and S~^-1 S (Figs. 2-4).
 
 Parity status of each function is listed in the module headers; every
 function listed is pinned by a ``-m "not gpu"`` test except where a module
