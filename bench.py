@@ -180,6 +180,22 @@ def cpu_baseline(which=0):
                       % (name, out["seconds"], out["true_residual"])}
 
 
+def replica_totals(dist, device, times_ms, steps, world):
+    """Whole-job numbers of N replicas: each rank solves the workload's
+    len(PERMS) * steps problems on its own GPU (no data exchange); the job
+    takes the slowest rank's time, so every elapsed time is the max over ranks
+    (one all-reduce), and the throughput is all ranks' solves over it.
+    Returns (max times in ms, solves per second for each)."""
+    times_ms = [float(t) for t in times_ms]
+    if dist is not None:
+        import torch
+        tt = torch.tensor(times_ms, dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        times_ms = [float(v) for v in tt]
+    solves = len(PERMS) * steps * world
+    return times_ms, [solves / (t / 1e3) for t in times_ms]
+
+
 def run_reference(args, rank, world):
     """The CPU oracle timed as the reference arm (rank 0 only)."""
     if rank != 0:
@@ -668,14 +684,7 @@ def main():
             mms += a.elapsed_time(b)
         mixed[name] = {"value": len(PERMS) * args.steps / (mms / 1e3), "unit": UNIT,
                        "ms_per_step": mms / args.steps, "max_true_residual": mworst}
-    if dist is not None:
-        tt = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(tt[0]), float(tt[1])
-
-    solves = len(PERMS) * args.steps * world
-    value = solves / (ms / 1e3)
-    e2e_value = solves / (e2e_ms / 1e3)
+    (ms, e2e_ms), (value, e2e_value) = replica_totals(dist, dev, (ms, e2e_ms), args.steps, world)
     if rank != 0:
         ctx.close()
         if dist is not None:
