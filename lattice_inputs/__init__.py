@@ -40,6 +40,7 @@ __all__ = [
     "point_sources",
     "training_gauge",
     "prepare_training_gauges",
+    "coupling_gauge",
     "workload_gauge",
     "random_su3",
 ]
@@ -368,6 +369,16 @@ def training_gauge(kind, index):
         return dims, cached("train_8p4_eps0.2_ape10_s%d" % seed,
                             lambda: ape_smear(random_gauge(dims, 0.2, seed), dims, 0.5, 10))
     raise KeyError(kind)
+
+
+def coupling_gauge(beta, index=0):
+    """8^4 plaquette-action field at coupling beta (200 Cabibbo-Marinari
+    sweeps from a cold start, seed 21 + index + 100 (beta - 5.4) rounded),
+    the stand-ins for the paper's beta = 5.4, 5.7, 5.9 ensembles (cached)."""
+    dims = (8, 8, 8, 8)
+    seed = 21 + int(index) + int(round(100 * (beta - 5.4)))
+    key = "coupling_8p4_b%.2f_s%d" % (beta, seed)
+    return dims, cached(key, lambda: heatbath_gauge(dims, beta, 200, seed))
 
 
 def _make_training_gauge(args):

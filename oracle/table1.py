@@ -1,0 +1,79 @@
+"""Table 1 of the paper on synthetic fields (oracle).
+
+Test infrastructure, like the rest of ``oracle/``; slow (minutes), not part
+of the test suite.
+
+Section 4 solves D x = f to 1e-8 at kappa = 1/6 (m0 = -1 with
+D = (m0 + 4) - 1/2 H) on lattices at beta = 5.4, 5.7, 5.9 with BiCGStab,
+plain and right-preconditioned by a 3-level V-cycle built on the Section 3
+approximation (coarsest level inverted exactly, the D_rr solves of every level
+by BiCGStab to 1e-2), with P_I^T for the first two couplings and P_II^T for
+the third, and reports the average convergence rate R of both.
+
+Stand-ins: the paper's ensembles are not available, so the fields are seeded
+8^4 plaquette-action heatbath fields (``lattice_inputs.coupling_gauge``); "8^8"
+is read as 8^4.  The condition number of the table's second row is read as
+the 2-norm condition number of D (``spectra.condition_number``: Lanczos on
+D^H D and on its inverse through one sparse LU of D).
+
+    python -m oracle.table1          prints one JSON line per coupling
+    python -m oracle.table1 --cond   adds the condition number of D and its
+                                     eigenvalue of smallest real part
+    python -m oracle.table1 --type1  also runs beta = 5.9 with P_I^T at both
+                                     levels (the case the paper reports as not
+                                     converging)
+"""
+from __future__ import annotations
+
+import json
+import time
+
+import numpy as np
+
+from . import dirac, krylov, permute, spectra, vcycle
+
+__all__ = ["run"]
+
+LEVELS = {
+    5.4: [(permute.TYPE_I, 0, True), (permute.TYPE_I, 0, True)],
+    5.7: [(permute.TYPE_I, 0, True), (permute.TYPE_I, 0, True)],
+    5.9: [(permute.TYPE_II, 0, True), (permute.TYPE_II, 1, True)],
+}
+
+
+def run(beta, m0=-1.0, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100, cond=False,
+        levels=None, plain=True, maxiter_pc=200):
+    import lattice_inputs as li
+    dims, U = li.coupling_gauge(beta)
+    D = dirac.wilson_matrix(U, dims, m0).tocsr()
+    f = li.gaussian_source(dims, seed_source).ravel()
+    out = {"beta": beta, "m0": m0, "dims": dims, "plaquette": li.average_plaquette(U, dims)}
+    if cond:
+        kappa, smin, smax = spectra.condition_number(D, tol=1e-6)
+        ev = spectra.leftmost_eigenvalues(D, k=2, tol=1e-6)
+        out["condition"] = {"kappa": kappa, "sigma_min": smin, "sigma_max": smax,
+                            "leftmost_eigenvalue": [float(ev[0].real), float(abs(ev[0].imag))]}
+    if plain:
+        t0 = time.time()
+        x, info = krylov.bicgstab(lambda v: D @ v, f, tol=tol, maxiter=maxiter)
+        out["plain"] = {"iters": info["iters"], "converged": info["converged"],
+                        "R": krylov.convergence_rate(info["history"]),
+                        "residual": float(np.linalg.norm(D @ x - f) / np.linalg.norm(f)),
+                        "seconds": time.time() - t0}
+    levels = LEVELS[beta] if levels is None else levels
+    t0 = time.time()
+    vc = vcycle.VCycle(D, dims, levels, schur="reusken", inner=inner_tol)
+    x, info = vcycle.preconditioned_bicgstab(D, f, vc, tol=tol, maxiter=maxiter_pc)
+    out["preconditioned"] = {"levels": [list(map(int, lv)) for lv in levels],
+                             "iters": info["iters"], "converged": info["converged"], "R": info["R"],
+                             "residual": float(np.linalg.norm(D @ x - f) / np.linalg.norm(f)),
+                             "seconds": time.time() - t0}
+    return out
+
+
+if __name__ == "__main__":
+    import sys
+    for b in (5.4, 5.7, 5.9):
+        print(json.dumps(run(b, cond="--cond" in sys.argv)), flush=True)
+    if "--type1" in sys.argv:
+        print(json.dumps(run(5.9, levels=LEVELS[5.4], plain=False, maxiter_pc=60)), flush=True)

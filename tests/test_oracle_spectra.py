@@ -21,3 +21,31 @@ def test_approximate_schur_spectrum_clusters_around_one_best_for_type_II():
         spread[name] = np.abs(ev - 1).mean()
     assert max(spread["P_II"], spread["P_II^T"]) < spread["P_I"]
     assert min(spread["P_II"], spread["P_II^T"]) <= spread["P_I^T"]
+
+
+def test_condition_number_matches_dense_svd():
+    """The Lanczos estimate (extreme eigenvalues of D^H D, small Krylov space
+    so that ARPACK restarts) equals the 2-norm condition number of a dense
+    SVD on a 2^4 and a 4x2x2x2 field."""
+    for dims, m0 in (((2, 2, 2, 2), -0.5), ((4, 2, 2, 2), -0.9)):
+        U = li.random_gauge(dims, 0.5, 7)
+        D = dirac.wilson_matrix(U, dims, m0).tocsr()
+        sv = np.linalg.svd(D.toarray(), compute_uv=False)
+        kappa, smin, smax = spectra.condition_number(D, tol=1e-12, ncv=24)
+        assert abs(smax - sv[0]) <= 1e-8 * sv[0]
+        assert abs(smin - sv[-1]) <= 1e-8 * sv[0]
+        assert abs(kappa - sv[0] / sv[-1]) <= 1e-7 * kappa
+
+
+def test_leftmost_eigenvalues_match_dense():
+    """Arnoldi's leftmost eigenvalues (restarted, small Krylov space) are the
+    dense spectrum's eigenvalues of smallest real part, on a 4x2x2x2 field."""
+    dims = (4, 2, 2, 2)
+    U = li.random_gauge(dims, 0.5, 8)
+    D = dirac.wilson_matrix(U, dims, -0.9).tocsr()
+    dense = np.linalg.eigvals(D.toarray())
+    want = np.sort(dense.real)[:4]
+    got = spectra.leftmost_eigenvalues(D, k=4, tol=1e-12, ncv=120)
+    assert np.allclose(np.sort(got.real), want, atol=1e-8)
+    for z in got:                                  # each is an eigenvalue of D
+        assert np.abs(dense - z).min() < 1e-8
