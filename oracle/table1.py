@@ -21,7 +21,10 @@ D^H D and on its inverse through one sparse LU of D).
                                      eigenvalue of smallest real part
     python -m oracle.table1 --type1  also runs beta = 5.9 with P_I^T at both
                                      levels (the case the paper reports as not
-                                     converging)
+                                     converging; 30 outer steps at most, the
+                                     rest-set solves capped at 2000 steps)
+    --kappa K (default 1/6, m0 = 1/(2K) - 4) and --beta B ... choose the
+    hopping parameter and the couplings.
 """
 from __future__ import annotations
 
@@ -42,7 +45,7 @@ LEVELS = {
 
 
 def run(beta, m0=-1.0, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100, cond=False,
-        levels=None, plain=True, maxiter_pc=200):
+        levels=None, plain=True, maxiter_pc=200, inner_maxiter=100000):
     import lattice_inputs as li
     dims, U = li.coupling_gauge(beta)
     D = dirac.wilson_matrix(U, dims, m0).tocsr()
@@ -62,18 +65,35 @@ def run(beta, m0=-1.0, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100, 
                         "seconds": time.time() - t0}
     levels = LEVELS[beta] if levels is None else levels
     t0 = time.time()
-    vc = vcycle.VCycle(D, dims, levels, schur="reusken", inner=inner_tol)
+    vc = vcycle.VCycle(D, dims, levels, schur="reusken", inner=inner_tol,
+                       inner_maxiter=inner_maxiter)
     x, info = vcycle.preconditioned_bicgstab(D, f, vc, tol=tol, maxiter=maxiter_pc)
     out["preconditioned"] = {"levels": [list(map(int, lv)) for lv in levels],
                              "iters": info["iters"], "converged": info["converged"], "R": info["R"],
                              "residual": float(np.linalg.norm(D @ x - f) / np.linalg.norm(f)),
+                             "inner_solves": len(vc.inner_log),
+                             "inner_steps_max": max((s for _, s, _ in vc.inner_log), default=0),
+                             "inner_not_converged": sum(1 for *_, c in vc.inner_log if not c),
                              "seconds": time.time() - t0}
     return out
 
 
+def _main(argv):
+    import argparse
+    ap = argparse.ArgumentParser(prog="python -m oracle.table1")
+    ap.add_argument("--cond", action="store_true")
+    ap.add_argument("--type1", action="store_true")
+    ap.add_argument("--kappa", type=float, default=1.0 / 6.0)
+    ap.add_argument("--beta", type=float, nargs="*", default=[5.4, 5.7, 5.9])
+    a = ap.parse_args(argv)
+    m0 = 1.0 / (2.0 * a.kappa) - 4.0
+    for b in a.beta:
+        print(json.dumps(run(b, m0=m0, cond=a.cond)), flush=True)
+    if a.type1:
+        print(json.dumps(run(5.9, m0=m0, levels=LEVELS[5.4], plain=False, maxiter_pc=30,
+                             inner_maxiter=2000)), flush=True)
+
+
 if __name__ == "__main__":
     import sys
-    for b in (5.4, 5.7, 5.9):
-        print(json.dumps(run(b, cond="--cond" in sys.argv)), flush=True)
-    if "--type1" in sys.argv:
-        print(json.dumps(run(5.9, levels=LEVELS[5.4], plain=False, maxiter_pc=60)), flush=True)
+    _main(sys.argv[1:])

@@ -67,10 +67,14 @@ def _approx_schur(A, perm, nb, schur):
 class VCycle:
     """levels: list of (ptype, mu, inv) for levels 0 .. L-2 (the last level is
     solved exactly).  inner: "direct" (sparse LU of A_rr) or a BiCGStab
-    tolerance (float) for the rest-set solves."""
+    tolerance (float) for the rest-set solves, each capped at inner_maxiter
+    steps (the last iterate is used if the cap is reached).  inner_log
+    collects (level, steps, converged) of every iterative rest-set solve."""
 
-    def __init__(self, D, dims, levels, schur="reusken", inner="direct"):
+    def __init__(self, D, dims, levels, schur="reusken", inner="direct", inner_maxiter=100000):
         self.inner = inner
+        self.inner_maxiter = int(inner_maxiter)
+        self.inner_log = []
         self.levels = []
         A = sp.csr_matrix(D)
         d = tuple(dims)
@@ -78,7 +82,8 @@ class VCycle:
             perm, nb = permute.permutation(d, ptype, mu, inv)
             blocks = partition(A, perm, nb)
             lu = sla.splu(blocks[3].tocsc()) if inner == "direct" else None
-            self.levels.append(dict(perm=np.asarray(perm), nb=nb, blocks=blocks, lu=lu))
+            self.levels.append(dict(index=len(self.levels), perm=np.asarray(perm), nb=nb,
+                                    blocks=blocks, lu=lu))
             A = _approx_schur(A, perm, nb, schur)
             d = coarse_dims(d, ptype, mu)
         self.coarsest = sla.splu(A.tocsc())
@@ -88,7 +93,9 @@ class VCycle:
         if lev["lu"] is not None:
             return lev["lu"].solve(v)
         Arr = lev["blocks"][3]
-        z, _ = krylov.bicgstab(lambda u: Arr @ u, v, tol=float(self.inner), maxiter=100000)
+        z, info = krylov.bicgstab(lambda u: Arr @ u, v, tol=float(self.inner),
+                                  maxiter=self.inner_maxiter)
+        self.inner_log.append((lev["index"], info["iters"], info["converged"]))
         return z
 
     def apply(self, f, level=0):
