@@ -150,6 +150,21 @@ def _ptr(t):
     return t.data_ptr()
 
 
+def _need(t, nbytes, what):
+    """Refuse a tensor smaller than the nbytes the call reads or writes
+    (GS_EINVAL), before any device access; raw integer pointers are the
+    caller's responsibility."""
+    if t is None or isinstance(t, int):
+        return
+    have = t.numel() * t.element_size()
+    if have < nbytes:
+        raise GschurError(GS_EINVAL, "%s holds %d bytes, the call needs %d" % (what, have, nbytes))
+
+
+SPINOR_BYTES = 192          # complex128 [4][3] per site
+LINK_BYTES = 4 * 9 * 16     # complex128 [4][3][3] per site
+
+
 def _check(ctx, status, allow=(GS_OK,)):
     if status not in allow:
         raise GschurError(status, gs_last_error(ctx))
@@ -418,13 +433,20 @@ class Context:
         except Exception:
             pass
 
+    def _need_lattice(self, nrhs=1, **tensors):
+        for name, t in tensors.items():
+            _need(t, nrhs * self.volume * SPINOR_BYTES, name)
+
     def set_gauge(self, U):
+        _need(U, self.volume * LINK_BYTES, "U")
         return gs_set_gauge(self.handle, U)
 
     def wilson_apply(self, x, y):
+        self._need_lattice(x=x, y=y)
         return wilson_apply(self.handle, x, y)
 
     def permute_sites(self, ptype, dir, inverse, transpose, x, y):
+        self._need_lattice(x=x, y=y)
         return permute_sites(self.handle, ptype, dir, inverse, transpose, x, y)
 
     def get_permutation(self, ptype, dir, inverse, perm):
@@ -434,9 +456,12 @@ class Context:
         return schur_apply(self.handle, ptype, dir, inverse, xb, yb, opts, allow)
 
     def schur_solve(self, ptype, dir, inverse, f, x, opts=None, allow=(GS_OK,)):
+        self._need_lattice(f=f, x=x)
         return schur_solve(self.handle, ptype, dir, inverse, f, x, opts, allow)
 
     def schur_solve_multi(self, ptype, dir, inverse, nrhs, f, x, opts=None, allow=(GS_OK,)):
+        if 1 <= int(nrhs) <= 32:            # other counts: the library reports GS_EINVAL
+            self._need_lattice(int(nrhs), f=f, x=x)
         return schur_solve_multi(self.handle, ptype, dir, inverse, nrhs, f, x, opts, allow)
 
     def lowp_pack_multi(self, ptype, dir, inverse, prec, nrhs, x, x_lp):

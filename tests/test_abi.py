@@ -52,3 +52,29 @@ def test_oracle_and_product_are_independent():
         if f.endswith((".py", ".c", ".h")):
             txt = open(os.path.join(ROOT, "oracle", f)).read()
             assert not re.search(r"(from|import)\s+paper_0704_2341_gb300|libgschur", txt), f
+
+
+def test_context_refuses_short_buffers_before_any_device_access():
+    """The binding checks every full-lattice buffer against the context's
+    volume (GS_EINVAL) before it forms a pointer, so a short tensor can never
+    reach a kernel; CPU tensors of the right size then fail at the pointer
+    check.  A context object without a device handle is enough for both."""
+    import torch
+    import paper_0704_2341_gb300 as gs
+    ctx = object.__new__(gs.Context)
+    ctx.dims, ctx.m0, ctx.handle = (4, 4, 2, 2), 0.1, None
+    ctx.volume = 64
+    short = torch.zeros(64 * 12 - 1, dtype=torch.complex128)
+    full = torch.zeros(64, 4, 3, dtype=torch.complex128)
+    for call in (lambda: ctx.wilson_apply(short, full), lambda: ctx.wilson_apply(full, short),
+                 lambda: ctx.permute_sites(1, 0, 0, 0, full, short),
+                 lambda: ctx.schur_solve(1, 0, 0, short, full),
+                 lambda: ctx.schur_solve_multi(1, 0, 0, 2, full, full),
+                 lambda: ctx.set_gauge(torch.zeros(64, 4, 3, 2, dtype=torch.complex128))):
+        with pytest.raises(gs.GschurError) as e:
+            call()
+        assert e.value.status == gs.GS_EINVAL
+    with pytest.raises(ValueError):                     # right size, but not on a GPU
+        ctx.wilson_apply(full, full.view(torch.float64))
+    with pytest.raises(ValueError):
+        ctx.set_gauge(torch.zeros(64, 4, 3, 3, dtype=torch.complex128))
