@@ -24,7 +24,9 @@ D^H D and on its inverse through one sparse LU of D).
                                      converging; 30 outer steps at most, the
                                      rest-set solves capped at 2000 steps)
     --kappa K (default 1/6, m0 = 1/(2K) - 4) and --beta B ... choose the
-    hopping parameter and the couplings.
+    hopping parameter and the couplings; --schur first uses the first-order
+    coarse operator (D_rr's couplings ignored) in the V-cycle; --no-plain
+    skips the unpreconditioned solve.
 """
 from __future__ import annotations
 
@@ -45,7 +47,7 @@ LEVELS = {
 
 
 def run(beta, m0=-1.0, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100, cond=False,
-        levels=None, plain=True, maxiter_pc=200, inner_maxiter=100000):
+        levels=None, plain=True, maxiter_pc=200, inner_maxiter=100000, schur="reusken"):
     import lattice_inputs as li
     dims, U = li.coupling_gauge(beta)
     D = dirac.wilson_matrix(U, dims, m0).tocsr()
@@ -65,10 +67,10 @@ def run(beta, m0=-1.0, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100, 
                         "seconds": time.time() - t0}
     levels = LEVELS[beta] if levels is None else levels
     t0 = time.time()
-    vc = vcycle.VCycle(D, dims, levels, schur="reusken", inner=inner_tol,
+    vc = vcycle.VCycle(D, dims, levels, schur=schur, inner=inner_tol,
                        inner_maxiter=inner_maxiter)
     x, info = vcycle.preconditioned_bicgstab(D, f, vc, tol=tol, maxiter=maxiter_pc)
-    out["preconditioned"] = {"levels": [list(map(int, lv)) for lv in levels],
+    out["preconditioned"] = {"levels": [list(map(int, lv)) for lv in levels], "schur": schur,
                              "iters": info["iters"], "converged": info["converged"], "R": info["R"],
                              "residual": float(np.linalg.norm(D @ x - f) / np.linalg.norm(f)),
                              "inner_solves": len(vc.inner_log),
@@ -85,10 +87,13 @@ def _main(argv):
     ap.add_argument("--type1", action="store_true")
     ap.add_argument("--kappa", type=float, default=1.0 / 6.0)
     ap.add_argument("--beta", type=float, nargs="*", default=[5.4, 5.7, 5.9])
+    ap.add_argument("--schur", default="reusken", choices=["reusken", "first"])
+    ap.add_argument("--no-plain", action="store_true")
     a = ap.parse_args(argv)
     m0 = 1.0 / (2.0 * a.kappa) - 4.0
     for b in a.beta:
-        print(json.dumps(run(b, m0=m0, cond=a.cond)), flush=True)
+        print(json.dumps(run(b, m0=m0, cond=a.cond, schur=a.schur, plain=not a.no_plain)),
+              flush=True)
     if a.type1:
         print(json.dumps(run(5.9, m0=m0, levels=LEVELS[5.4], plain=False, maxiter_pc=30,
                              inner_maxiter=2000)), flush=True)

@@ -24,7 +24,9 @@ Readings (the paper gives the recipe, not its bookkeeping):
     coarse lattice's own site order);
   * ``schur="exact"`` uses the exact Schur complement at every level (then a
     V-cycle with exact inner solves is D^-1: the pin), ``schur="reusken"``
-    the Section 3 approximation.
+    the Section 3 approximation, ``schur="first"`` its first-order truncation
+    M = d^-1 (the approximation that ignores D_rr's couplings, which Section
+    3 cites as earlier work), a cheap baseline.
 
 The average convergence rate R of Section 4 is ``krylov.convergence_rate``
 of the (preconditioned) BiCGStab residual history.
@@ -56,9 +58,12 @@ def _approx_schur(A, perm, nb, schur):
     if schur == "exact":
         X = np.linalg.solve(Arr.toarray(), Arb.toarray())
         return sp.csr_matrix(Abb.toarray() - Abr.toarray() @ X)
-    op = reusken.ReuskenOperator.from_blocks(Abb, Abr, Arb, Arr)
+    order = {"reusken": 2, "first": 1}[schur]
+    op = reusken.ReuskenOperator.from_blocks(Abb, Abr, Arb, Arr, order=order)
     n = op.n_r
     dinv = sp.bsr_matrix((op.dinv, np.arange(n), np.arange(n + 1)), shape=Arr.shape).tocsr()
+    if order == 1:
+        return (Abb - Abr @ dinv @ Arb).tocsr()
     dtinv = sp.bsr_matrix((op.dtinv, np.arange(n), np.arange(n + 1)), shape=Arr.shape).tocsr()
     M = dinv + dtinv - dinv @ Arr @ dtinv
     return (Abb - Abr @ M @ Arb).tocsr()

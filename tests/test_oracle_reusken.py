@@ -87,3 +87,46 @@ def test_free_field_type_I_row_sums_closed_form():
         g = dirac.GAMMA[mu]
         expect = expect - 0.5 * np.kron((np.eye(4) - g) + (np.eye(4) + g), np.eye(3))
     assert np.abs(dt[k] - expect).max() <= 1e-13
+
+
+def test_first_order_truncation_error_is_first_order_in_the_hopping():
+    """order=1 (M = d^-1, D_rr's couplings ignored): D_rr^-1 - d^-1 = O(t), so
+    ||S - S_1|| / ||S - D_bb|| halves with t, while the Section 3 formula's
+    ratio falls by four and stays below it (P_II^T, direction 1, whose D_bb
+    and D_rr both have hops)."""
+    dims = (4, 4, 4, 4)
+    U = li.random_gauge(dims, 0.4, 5)
+    m0 = 0.3
+    D1 = dirac.wilson_matrix(U, dims, m0).tocsr()
+    diag = (m0 + 4.0) * sp.identity(D1.shape[0], format="csr")
+    H = D1 - diag
+    perm, nb = permute.permutation(dims, permute.TYPE_II, 1, True)
+    e1, e2 = [], []
+    for tt in (0.4, 0.2, 0.1):
+        D = (diag + tt * H).tocsr()
+        S = schur.schur_dense(D, perm, nb)
+        Dbb = schur.partition(D, perm, nb)[0].toarray()
+        den = np.linalg.norm(S - Dbb)
+        e1.append(np.linalg.norm(S - reusken.reusken_dense(D, perm, nb, order=1)) / den)
+        e2.append(np.linalg.norm(S - reusken.reusken_dense(D, perm, nb, order=2)) / den)
+    for a, b in zip(e1, e1[1:]):
+        assert 0.4 < b / a < 0.6, e1
+    for a, b in zip(e2, e2[1:]):
+        assert 0.15 < b / a < 0.35, e2
+    assert all(x2 < x1 for x1, x2 in zip(e1, e2))
+
+
+def test_first_order_is_d_inverse_for_wilson():
+    """For the Wilson D the site-block diagonal of D_rr is (m0 + 4) 1, so the
+    first-order operator is D_bb - D_br D_rb / (m0 + 4) exactly."""
+    dims = (4, 4, 2, 4)
+    U = li.random_gauge(dims, 0.3, 6)
+    m0 = -0.3
+    D = dirac.wilson_matrix(U, dims, m0).tocsr()
+    perm, nb = permute.permutation(dims, permute.TYPE_I, 0, True)
+    Dbb, Dbr, Drb, _ = schur.partition(D, perm, nb)
+    want = Dbb.toarray() - (Dbr @ Drb).toarray() / (m0 + 4.0)
+    got = reusken.reusken_dense(D, perm, nb, order=1)
+    assert np.abs(got - want).max() <= 1e-13
+    with pytest.raises(ValueError):
+        reusken.ReuskenOperator(D, perm, nb, order=3)

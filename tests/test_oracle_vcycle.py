@@ -60,3 +60,25 @@ def test_inexact_vcycle_true_residual():
     x, info = vcycle.preconditioned_bicgstab(D, f, vc, tol=1e-8, maxiter=200)
     assert info["converged"]
     assert np.linalg.norm(D @ x - f) <= 1e-7 * np.linalg.norm(f)
+
+
+def test_first_order_vcycle_is_a_weaker_preconditioner():
+    """The first-order coarse operator (D_rr's couplings ignored) keeps a
+    sparser coarsest level and still preconditions, but the Section 3
+    second-order one converges faster (measured here: 10 steps, R = 0.15
+    against 6 steps, R = 0.04)."""
+    dims = (8, 8, 4, 4)
+    U = li.random_gauge(dims, 0.3, 1)
+    D = dirac.wilson_matrix(U, dims, -0.2).tocsr()
+    f = li.gaussian_source(dims, 100).ravel()
+    lv = [(II, 0, True), (II, 1, True)]
+    out = {}
+    for sc in ("first", "reusken"):
+        vc = vcycle.VCycle(D, dims, lv, schur=sc)
+        x, info = vcycle.preconditioned_bicgstab(D, f, vc, tol=1e-8, maxiter=100)
+        assert info["converged"]
+        assert np.linalg.norm(D @ x - f) <= 1e-7 * np.linalg.norm(f)
+        out[sc] = (info["iters"], info["R"], vc.coarse_op.nnz)
+    assert out["reusken"][0] < out["first"][0] <= 20
+    assert out["reusken"][1] < out["first"][1] < 0.3
+    assert out["first"][2] < out["reusken"][2]
