@@ -23,7 +23,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["bicgstab", "gmres", "convergence_rate"]
+__all__ = ["bicgstab", "gmres", "convergence_rate", "mean_ratio"]
 
 
 def _norm(v):
@@ -146,3 +146,14 @@ def convergence_rate(history):
     if h.size < 2:
         return 0.0
     return float((h[-1] / h[0]) ** (1.0 / (h.size - 1)))
+
+
+def mean_ratio(history):
+    """The other reading of Section 4's R: the arithmetic mean of the ratios
+    ||r_{k+1}|| / ||r_k|| over the recorded history (never below the
+    geometric mean, equal to it for a geometric sequence)."""
+    h = np.asarray(history, dtype=float)
+    h = h[h > 0]
+    if h.size < 2:
+        return 0.0
+    return float(np.mean(h[1:] / h[:-1]))

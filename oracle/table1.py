@@ -63,6 +63,7 @@ def run(beta, m0=-1.0, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100, 
         x, info = krylov.bicgstab(lambda v: D @ v, f, tol=tol, maxiter=maxiter)
         out["plain"] = {"iters": info["iters"], "converged": info["converged"],
                         "R": krylov.convergence_rate(info["history"]),
+                        "R_arith": krylov.mean_ratio(info["history"]),
                         "residual": float(np.linalg.norm(D @ x - f) / np.linalg.norm(f)),
                         "seconds": time.time() - t0}
     levels = LEVELS[beta] if levels is None else levels
@@ -72,6 +73,7 @@ def run(beta, m0=-1.0, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100, 
     x, info = vcycle.preconditioned_bicgstab(D, f, vc, tol=tol, maxiter=maxiter_pc)
     out["preconditioned"] = {"levels": [list(map(int, lv)) for lv in levels], "schur": schur,
                              "iters": info["iters"], "converged": info["converged"], "R": info["R"],
+                             "R_arith": krylov.mean_ratio(info["history"]),
                              "residual": float(np.linalg.norm(D @ x - f) / np.linalg.norm(f)),
                              "inner_solves": len(vc.inner_log),
                              "inner_steps_max": max((s for _, s, _ in vc.inner_log), default=0),

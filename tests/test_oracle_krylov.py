@@ -72,3 +72,16 @@ def test_gmres_first_cycle_minimises_residual():
         K = np.stack([np.linalg.matrix_power(Ad, i) @ b for i in range(k)], 1)
         c = np.linalg.lstsq(Ad @ K, b, rcond=None)[0]
         assert np.linalg.norm(x - K @ c) <= 1e-9 * np.linalg.norm(x)
+
+
+def test_mean_ratio_against_geometric_rate():
+    """Arithmetic mean of successive ratios: equals the geometric rate on a
+    geometric sequence and exceeds it otherwise (AM-GM); worked example
+    1, 0.5, 0.05: ratios 0.5 and 0.1, mean 0.3, geometric sqrt(0.05)."""
+    h = [1.0 * 0.3 ** k for k in range(8)]
+    assert krylov.mean_ratio(h) == pytest.approx(0.3)
+    assert krylov.convergence_rate(h) == pytest.approx(0.3)
+    h = [1.0, 0.5, 0.05]
+    assert krylov.mean_ratio(h) == pytest.approx(0.3)
+    assert krylov.convergence_rate(h) == pytest.approx(0.05 ** 0.5)
+    assert krylov.mean_ratio([2.0]) == 0.0
