@@ -23,7 +23,10 @@ Everything here is complex128 and written for clarity, not speed:
                  Section 3 (site-block diagonal d and row sums d~);
 * ``vcycle``  -- the cyclic-reduction V-cycle preconditioner of Section 4
                  built from it, and BiCGStab preconditioned by it (R);
-* ``spectra`` -- dense spectra of S, S~ and S~^-1 S (Figs. 2-4).
+* ``spectra`` -- dense spectra of S, S~ and S~^-1 S (Figs. 2-4), and the
+                 condition number and leftmost eigenvalues of a sparse D;
+* ``table1``  -- the Section 4 experiment of Table 1 on seeded stand-in
+                 fields (a script: ``python -m oracle.table1``).
 
 Parity status of each function is listed in the module headers; every
 function listed is pinned by a ``-m "not gpu"`` test except where a module

@@ -1,5 +1,7 @@
 """Wilson-Dirac operator, assembled as a sparse matrix (oracle).
 
+Test infrastructure, like the rest of ``oracle/``.
+
 The paper blocks "the Wilson-Dirac operator" (Section 2, around Fig. 2), calls
 its off-diagonal part the "hopping matrix" and quotes the hopping parameter
 kappa (Section 3 and Section 4), but never writes the operator out.  The

@@ -1,5 +1,7 @@
 """Textbook Krylov solvers (oracle).
 
+Test infrastructure, like the rest of ``oracle/``.
+
 The paper's solver is "vanilla BiCGstab" (Section 4); the 8^4 workload asks
 for restarted GMRES(30) on S_bb.  Both are written out below exactly as in
 their original papers, in complex arithmetic, with the convergence test on

@@ -1,5 +1,7 @@
 """Gauge-equivariant linear convolutional network (oracle).
 
+Test infrastructure, like the rest of ``oracle/``.
+
 The learned preconditioner M ~ D_rr^-1 used inside flexible GMRES for the
 inner solve.  (The paper's own preconditioner is the Reusken approximation
 and a V-cycle, Section 4; the learned one replaces the hand-made

@@ -1,5 +1,7 @@
 """Site permutations of the paper (oracle).
 
+Test infrastructure, like the rest of ``oracle/``.
+
 Section 2: ``Permutation_block`` returns a permutation operator P(p) that
 exchanges the rows of D, with p chosen so that the coarse-lattice sites are
 labelled first (Fig. 1, a 4x4 example whose picture is lost).  Two types are

@@ -1,5 +1,7 @@
 """Partition, Schur complement, apply and solve (oracle).
 
+Test infrastructure, like the rest of ``oracle/``.
+
 Section 1 of the paper: after permuting the sites so that the coarse set b
 comes first, D is split into the 2x2 block operator
 
