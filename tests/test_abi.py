@@ -78,3 +78,33 @@ def test_context_refuses_short_buffers_before_any_device_access():
         ctx.wilson_apply(full, full.view(torch.float64))
     with pytest.raises(ValueError):
         ctx.set_gauge(torch.zeros(64, 4, 3, 3, dtype=torch.complex128))
+
+
+def test_argument_checks_come_before_any_cuda_call():
+    """gs_create and wilson_apply_noalloc validate their arguments on the host
+    first: bad extents, a non-finite mass or a lattice past the index range
+    give GS_EINVAL, a lattice past the no-allocation scratch GS_ETOOLARGE,
+    all without a device; well-formed arguments then reach CUDA and, with no
+    GPU, give GS_ECUDA."""
+    import ctypes as ct
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_0704_2341_gb300 as gs
+    lib = gs._binding.lib
+
+    def create(dims, m0):
+        h = ct.c_void_p()
+        return lib.gs_create(ct.byref(h), (ct.c_int * 4)(*dims), ct.c_double(m0), None)
+
+    assert create((1, 4, 4, 4), 0.1) == gs.GS_EINVAL
+    assert create((4, 4, 0, 4), 0.1) == gs.GS_EINVAL
+    assert create((4, 4, 4, 4), float("nan")) == gs.GS_EINVAL
+    assert create((1024, 1024, 64, 64), 0.1) == gs.GS_EINVAL      # V * 12 >= 2^31
+    assert create((4, 4, 4, 4), 0.1) == gs._binding.GS_ECUDA
+    fake = 256                                   # never dereferenced: rejected first
+    assert gs.wilson_apply_noalloc((4, 4, 1, 4), 0.1, fake, fake, fake) == gs.GS_EINVAL
+    assert gs.wilson_apply_noalloc((4, 4, 4, 4), float("inf"), fake, fake, fake) == gs.GS_EINVAL
+    assert gs.wilson_apply_noalloc((16, 16, 16, 16), 0.1, fake, fake, fake) == \
+        gs._binding.GS_ETOOLARGE
+    assert gs.gs_last_error(None) == "null context"
