@@ -26,7 +26,8 @@ D^H D and on its inverse through one sparse LU of D).
     --kappa K (default 1/6, m0 = 1/(2K) - 4) and --beta B ... choose the
     hopping parameter and the couplings; --schur first uses the first-order
     coarse operator (D_rr's couplings ignored) in the V-cycle; --no-plain
-    skips the unpreconditioned solve.
+    skips the unpreconditioned solve; --index I ... runs further stand-in
+    fields of each coupling (other heatbath seeds).
 """
 from __future__ import annotations
 
@@ -47,12 +48,14 @@ LEVELS = {
 
 
 def run(beta, m0=-1.0, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100, cond=False,
-        levels=None, plain=True, maxiter_pc=200, inner_maxiter=100000, schur="reusken"):
+        levels=None, plain=True, maxiter_pc=200, inner_maxiter=100000, schur="reusken",
+        index=0):
     import lattice_inputs as li
-    dims, U = li.coupling_gauge(beta)
+    dims, U = li.coupling_gauge(beta, index)
     D = dirac.wilson_matrix(U, dims, m0).tocsr()
     f = li.gaussian_source(dims, seed_source).ravel()
-    out = {"beta": beta, "m0": m0, "dims": dims, "plaquette": li.average_plaquette(U, dims)}
+    out = {"beta": beta, "m0": m0, "dims": dims, "field_index": index,
+           "plaquette": li.average_plaquette(U, dims)}
     if cond:
         kappa, smin, smax = spectra.condition_number(D, tol=1e-6)
         ev = spectra.leftmost_eigenvalues(D, k=2, tol=1e-6)
@@ -91,11 +94,14 @@ def _main(argv):
     ap.add_argument("--beta", type=float, nargs="*", default=[5.4, 5.7, 5.9])
     ap.add_argument("--schur", default="reusken", choices=["reusken", "first"])
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--index", type=int, nargs="*", default=[0],
+                    help="stand-in field indices per coupling (seeds differ)")
     a = ap.parse_args(argv)
     m0 = 1.0 / (2.0 * a.kappa) - 4.0
     for b in a.beta:
-        print(json.dumps(run(b, m0=m0, cond=a.cond, schur=a.schur, plain=not a.no_plain)),
-              flush=True)
+        for i in a.index:
+            print(json.dumps(run(b, m0=m0, cond=a.cond, schur=a.schur, plain=not a.no_plain,
+                                 index=i)), flush=True)
     if a.type1:
         print(json.dumps(run(5.9, m0=m0, levels=LEVELS[5.4], plain=False, maxiter_pc=30,
                              inner_maxiter=2000)), flush=True)
