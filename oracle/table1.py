@@ -38,7 +38,7 @@ import numpy as np
 
 from . import dirac, krylov, permute, spectra, vcycle
 
-__all__ = ["run"]
+__all__ = ["run", "run_field", "LEVELS"]
 
 LEVELS = {
     5.4: [(permute.TYPE_I, 0, True), (permute.TYPE_I, 0, True)],
@@ -47,15 +47,26 @@ LEVELS = {
 }
 
 
-def run(beta, m0=-1.0, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100, cond=False,
-        levels=None, plain=True, maxiter_pc=200, inner_maxiter=100000, schur="reusken",
-        index=0):
+def run(beta, m0=-1.0, index=0, levels=None, **kw):
+    """One Table 1 column on the stand-in field of coupling beta (``index``
+    picks another heatbath seed); keywords as for ``run_field``."""
     import lattice_inputs as li
     dims, U = li.coupling_gauge(beta, index)
+    out = {"beta": beta, "field_index": index, "plaquette": li.average_plaquette(U, dims)}
+    out.update(run_field(U, dims, m0, LEVELS[beta] if levels is None else levels, **kw))
+    return out
+
+
+def run_field(U, dims, m0, levels, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100,
+              cond=False, plain=True, maxiter_pc=200, inner_maxiter=100000, schur="reusken"):
+    """Section 4's comparison on one field: plain BiCGStab and BiCGStab with
+    the V-cycle (levels: (ptype, mu, inverse) per coarsening) for D x = f, f a
+    Gaussian source, each to tol; reports steps, R (geometric and arithmetic
+    mean of the residual ratios) and the true residual of the returned x."""
+    import lattice_inputs as li
     D = dirac.wilson_matrix(U, dims, m0).tocsr()
     f = li.gaussian_source(dims, seed_source).ravel()
-    out = {"beta": beta, "m0": m0, "dims": dims, "field_index": index,
-           "plaquette": li.average_plaquette(U, dims)}
+    out = {"m0": m0, "dims": list(dims)}
     if cond:
         kappa, smin, smax = spectra.condition_number(D, tol=1e-6)
         ev = spectra.leftmost_eigenvalues(D, k=2, tol=1e-6)
@@ -69,7 +80,6 @@ def run(beta, m0=-1.0, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_source=100, 
                         "R_arith": krylov.mean_ratio(info["history"]),
                         "residual": float(np.linalg.norm(D @ x - f) / np.linalg.norm(f)),
                         "seconds": time.time() - t0}
-    levels = LEVELS[beta] if levels is None else levels
     t0 = time.time()
     vc = vcycle.VCycle(D, dims, levels, schur=schur, inner=inner_tol,
                        inner_maxiter=inner_maxiter)
