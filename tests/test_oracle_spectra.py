@@ -18,6 +18,11 @@ def test_approximate_schur_spectrum_clusters_around_one_best_for_type_II():
         ev_S, ev_St, ev = spectra.spectra(D, perm, nb)
         assert ev_S.size == ev_St.size == ev.size == nb * 12
         assert np.abs(ev - 1).max() < 0.1            # clustered around one
+        # det(S~^-1 S) = det S / det S~: the three spectra belong together
+        lhs = np.log(np.abs(ev)).sum()
+        rhs = np.log(np.abs(ev_S)).sum() - np.log(np.abs(ev_St)).sum()
+        assert abs(lhs - rhs) <= 1e-8 * max(1.0, abs(rhs))
+        assert abs(rhs) > 1e-3                       # S and S~ differ in determinant
         spread[name] = np.abs(ev - 1).mean()
     assert max(spread["P_II"], spread["P_II^T"]) < spread["P_I"]
     assert min(spread["P_II"], spread["P_II^T"]) <= spread["P_I^T"]
@@ -45,7 +50,9 @@ def test_leftmost_eigenvalues_match_dense():
     D = dirac.wilson_matrix(U, dims, -0.9).tocsr()
     dense = np.linalg.eigvals(D.toarray())
     want = np.sort(dense.real)[:4]
-    got = spectra.leftmost_eigenvalues(D, k=4, tol=1e-12, ncv=120)
-    assert np.allclose(np.sort(got.real), want, atol=1e-8)
-    for z in got:                                  # each is an eigenvalue of D
-        assert np.abs(dense - z).min() < 1e-8
+    for ncv in (120, 400):                         # Arnoldi, then the dense branch
+        got = spectra.leftmost_eigenvalues(D, k=4, tol=1e-12, ncv=ncv)
+        assert np.all(np.diff(got.real) >= -1e-12)  # returned by real part
+        assert np.allclose(got.real, want, atol=1e-8)
+        for z in got:                              # each is an eigenvalue of D
+            assert np.abs(dense - z).min() < 1e-8

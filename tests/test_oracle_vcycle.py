@@ -82,3 +82,19 @@ def test_first_order_vcycle_is_a_weaker_preconditioner():
     assert out["reusken"][0] < out["first"][0] <= 20
     assert out["reusken"][1] < out["first"][1] < 0.3
     assert out["first"][2] < out["reusken"][2]
+
+
+def test_coarse_operators_equal_the_approximation_columns():
+    """The sparse coarse operator a V-cycle level builds equals, column by
+    column, the operator of the Section 3 approximation (second order) or of
+    its first-order truncation, on two permutation types."""
+    from oracle import reusken
+    dims = (4, 4, 2, 2)
+    U = li.random_gauge(dims, 0.4, 9)
+    D = dirac.wilson_matrix(U, dims, 0.1).tocsr()
+    for t, mu, inv in ((II, 1, True), (I, 0, False)):
+        perm, nb = permute.permutation(dims, t, mu, inv)
+        for sc, order in (("reusken", 2), ("first", 1)):
+            A = vcycle._approx_schur(D, perm, nb, sc).toarray()
+            B = reusken.reusken_dense(D, perm, nb, order=order)
+            assert np.abs(A - B).max() <= 1e-13 * np.abs(B).max()
