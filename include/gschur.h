@@ -141,7 +141,8 @@ gs_status gs_set_gauge(gs_ctx* ctx, const void* U_dev);
  * direction (four partial sums combined in shared memory).  gs_get_option
  * returns the forced value, or under autotuning the variant chosen most
  * recently. */
-enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 3, GS_OPT_MULTI_BATCH = 4 };
+enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 3, GS_OPT_MULTI_BATCH = 4,
+       GS_OPT_WAIT_LIMIT_US = 5 };
 /* GS_OPT_INNER_KERNEL: 0 = each inner BiCGStab solve runs as one persistent
  * cooperative kernel (grid barriers with bounded waits between its phases;
  * the default), 1 = five kernel launches per iteration with the convergence
@@ -155,9 +156,24 @@ enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 
  * problem) shapes its work: 0 = the sources of a problem share every launch
  * when the rest set has at most 16384 sites, where one source leaves the GPU
  * latency bound, else they are solved one at a time by the single-source
- * solver (the default); 1 = always together; 2 = always one at a time. */
+ * solver (the default); 1 = always together; 2 = always one at a time.
+ * GS_OPT_WAIT_LIMIT_US: the bound, in microseconds (1 .. 60000000), on every
+ * device-side wait of the context's kernels -- the grid barriers of the
+ * persistent solvers and the mbarrier waits of the tensor-core network
+ * kernels [1000000, i.e. 1 s].  A wait that runs out makes its kernel stop,
+ * release what it holds (tensor memory) and report GS_TIMEOUT; the context
+ * stays usable. */
 gs_status gs_set_option(gs_ctx* ctx, int option, int value);
 gs_status gs_get_option(gs_ctx* ctx, int option, int* value);
+
+/* Failure-detection self-test of the bounded device waits (the paper has no
+ * counterpart).  which = 0: a two-block cooperative kernel in which one block
+ * never arrives at the persistent solvers' grid barrier; which = 1: one
+ * thread waits on an mbarrier that nothing arrives at.  Either wait runs out
+ * after the context's GS_OPT_WAIT_LIMIT_US, the kernel returns, and the call
+ * returns GS_TIMEOUT (the intended outcome; gs_last_error says so).  No fault
+ * and no hang: every wait involved is bounded.  Synchronises the stream. */
+gs_status gs_selftest_wait(gs_ctx* ctx, int which);
 
 /* Fill opts with the defaults listed in gs_solve_opts. */
 void gs_default_opts(gs_solve_opts* opts);
@@ -220,9 +236,11 @@ gs_status schur_solve(gs_ctx* ctx, int type, int dir, int inverse,
  * Larger lattices return GS_ETOOLARGE.  Every call overwrites the whole
  * table it uses, so no state carries over between calls; but all calls on a
  * device share the one array, so calls whose GPU work overlaps (e.g. on two
- * streams at once) race.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture. */
+ * streams at once) race.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) in the current device's context; the first call on a
+ * device also loads the library's module there, so make that first call
+ * before any stream capture.  Undersized buffers are not detected here: the
+ * caller guarantees the sizes above (the Python binding checks them). */
 gs_status wilson_apply_noalloc(const int dims[4], double m0, const void* U_dev,
                                const void* x_dev, void* y_dev, void* stream);
 
@@ -338,6 +356,16 @@ gs_status wilson_apply_lowp_multi(gs_ctx* ctx, int type, int dir, int inverse, i
  * except for that first call. */
 gs_status schur_apply_reusken(gs_ctx* ctx, int type, int dir, int inverse, const void* xb_dev,
                               void* yb_dev);
+
+/* y_b = S~_bb x_b with the approximation of the given order (Section 3):
+ * order 2 is schur_apply_reusken; order 1 is the cruder approximation that
+ * Section 3 cites as earlier work, which ignores the couplings inside D_rr:
+ * D_rr is replaced by its diagonal d = (m0 + 4) 1, so
+ *   S~_bb = D_bb - D_br D_rb / (m0 + 4)
+ * (two stencil launches and a scaling; no set-up).  Vectors and workspace as
+ * for schur_apply_reusken; asynchronous (order 2: except its first call). */
+gs_status schur_apply_approx(gs_ctx* ctx, int type, int dir, int inverse, int order,
+                             const void* xb_dev, void* yb_dev);
 
 /* z = D_rr^-1 t on the rest set of (type, dir, inverse): the inner solve of
  * S_bb on its own (opts->inner_tol, inner_prec, inner_solver as for

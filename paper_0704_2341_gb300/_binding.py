@@ -22,7 +22,8 @@ GS_TYPE_I, GS_TYPE_II = 1, 2
 GS_F64, GS_F32, GS_BF16 = 0, 1, 2
 GS_GMRES, GS_BICGSTAB = 0, 1
 GS_INNER_BICGSTAB, GS_INNER_FGMRES_NET = 0, 1
-GS_OPT_STENCIL_VARIANT, GS_OPT_INNER_KERNEL, GS_OPT_NET_KERNEL, GS_OPT_MULTI_BATCH = 1, 2, 3, 4
+GS_OPT_STENCIL_VARIANT, GS_OPT_INNER_KERNEL, GS_OPT_NET_KERNEL, GS_OPT_MULTI_BATCH, \
+    GS_OPT_WAIT_LIMIT_US = 1, 2, 3, 4, 5
 GS_PROF_STENCIL_F64, GS_PROF_STENCIL_F32, GS_PROF_STENCIL_BF16, GS_PROF_SOLVER_F64, \
     GS_PROF_SOLVER_LP = range(5)
 
@@ -34,7 +35,8 @@ EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson
            "gs_get_option", "schur_solve_multi", "schur_solve_batched", "gs_lowp_pack_multi",
            "gs_lowp_unpack_multi", "wilson_apply_lowp_multi", "gs_solve_rr", "gs_net_create",
            "gs_net_destroy", "gs_net_set_weights", "gs_net_get", "gs_net_apply",
-           "gs_net_train_step", "gs_set_net", "gs_profile_phases", "schur_apply_reusken")
+           "gs_net_train_step", "gs_set_net", "gs_profile_phases", "schur_apply_reusken",
+           "gs_selftest_wait", "schur_apply_approx")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -107,6 +109,8 @@ def _load():
         "gs_set_net": (i32, [vp, vp]),
         "gs_profile_phases": (i32, [vp, ctypes.POINTER(ctypes.c_double), i32]),
         "schur_apply_reusken": (i32, [vp, i32, i32, i32, vp, vp]),
+        "gs_selftest_wait": (i32, [vp, i32]),
+        "schur_apply_approx": (i32, [vp, i32, i32, i32, i32, vp, vp]),
         "schur_solve_multi": (i32, [vp, i32, i32, i32, i32, vp, vp, ctypes.POINTER(gs_solve_opts),
                                     ctypes.POINTER(gs_solve_stats)]),
         "schur_solve_batched": (i32, [i32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
@@ -241,10 +245,37 @@ def schur_solve(ctx, ptype, dir, inverse, f, x, opts=None, allow=(GS_OK,)):
     return st
 
 
+NOALLOC_MAX_SITES = 8192    # the static scratch of wilson_apply_noalloc
+
+
+def _need_c128(t, what):
+    """Refuse a tensor that is not complex128 (GS_EINVAL)."""
+    if t is None or isinstance(t, int):
+        return
+    import torch
+    if t.dtype != torch.complex128:
+        raise GschurError(GS_EINVAL, "%s must be complex128, not %s" % (what, t.dtype))
+
+
 def wilson_apply_noalloc(dims, m0, U, x, y, stream=None):
-    """y = D x without a context and without allocating (returns the status)."""
-    d = (ctypes.c_int * 4)(*[int(L) for L in dims])
-    return lib.wilson_apply_noalloc(d, float(m0), _ptr(U), _ptr(x), _ptr(y), stream)
+    """y = D x without a context and without allocating.  Returns the status;
+    extents the library rejects come back as GS_EINVAL / GS_ETOOLARGE, and
+    tensors that are smaller than the lattice needs or not complex128 raise
+    GschurError(GS_EINVAL) before any pointer reaches the library."""
+    d = [int(L) for L in dims]
+    if len(d) != 4 or min(d) < 2:
+        return GS_EINVAL
+    V = 1
+    for L in d:
+        if L > NOALLOC_MAX_SITES // V:
+            return GS_ETOOLARGE
+        V *= L
+    for t, nbytes, what in ((U, V * LINK_BYTES, "U"), (x, V * SPINOR_BYTES, "x"),
+                            (y, V * SPINOR_BYTES, "y")):
+        _need_c128(t, what)
+        _need(t, nbytes, what)
+    return lib.wilson_apply_noalloc((ctypes.c_int * 4)(*d), float(m0), _ptr(U), _ptr(x),
+                                    _ptr(y), stream)
 
 
 def gs_profile(ctx, enable):
@@ -253,6 +284,17 @@ def gs_profile(ctx, enable):
 
 def schur_apply_reusken(ctx, ptype, dir, inverse, xb, yb):
     return _check(ctx, lib.schur_apply_reusken(ctx, ptype, dir, int(bool(inverse)), _ptr(xb), _ptr(yb)))
+
+
+def schur_apply_approx(ctx, ptype, dir, inverse, order, xb, yb):
+    return _check(ctx, lib.schur_apply_approx(ctx, ptype, dir, int(bool(inverse)), int(order),
+                                              _ptr(xb), _ptr(yb)))
+
+
+def gs_selftest_wait(ctx, which):
+    """Run a bounded device wait that is meant to run out; returns the status
+    (GS_TIMEOUT is the intended outcome)."""
+    return lib.gs_selftest_wait(ctx, int(which))
 
 
 def gs_profile_phases(ctx):
@@ -482,8 +524,14 @@ class Context:
     def profile_phases(self):
         return gs_profile_phases(self.handle)
 
+    def selftest_wait(self, which):
+        return gs_selftest_wait(self.handle, which)
+
     def schur_apply_reusken(self, ptype, dir, inverse, xb, yb):
         return schur_apply_reusken(self.handle, ptype, dir, inverse, xb, yb)
+
+    def schur_apply_approx(self, ptype, dir, inverse, order, xb, yb):
+        return schur_apply_approx(self.handle, ptype, dir, inverse, order, xb, yb)
 
     def solve_rr(self, ptype, dir, inverse, t, z, opts=None, allow=(GS_OK,)):
         return gs_solve_rr(self.handle, ptype, dir, inverse, t, z, opts, allow)

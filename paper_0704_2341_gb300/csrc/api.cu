@@ -76,12 +76,15 @@ const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "null c
 gs_status gs_create(gs_ctx** out, const int dims[4], double m0, void* stream) {
     if (!out || !dims) return GS_EINVAL;
     *out = nullptr;
+    // V * 12 < 2^31; each extent is checked against what is left of that bound
+    // before it multiplies V, so the product cannot overflow
+    const int64_t kMaxSites = (((int64_t)1 << 31) - 1) / kSiteC;
     int64_t V = 1;
     for (int mu = 0; mu < 4; ++mu) {
-        if (dims[mu] < 2) return GS_EINVAL;
+        if (dims[mu] < 2 || dims[mu] > kMaxSites / V) return GS_EINVAL;
         V *= dims[mu];
     }
-    if (V * kSiteC >= ((int64_t)1 << 31) || !isfinite(m0)) return GS_EINVAL;
+    if (!isfinite(m0)) return GS_EINVAL;
     gs_ctx* c = new gs_ctx();
     for (int mu = 0; mu < 4; ++mu) c->dims[mu] = dims[mu];
     c->V = V;
@@ -201,6 +204,12 @@ gs_status gs_set_option(gs_ctx* c, int option, int value) {
         c->opt_multi_batch = value;
         return GS_OK;
     }
+    if (option == GS_OPT_WAIT_LIMIT_US) {
+        if (value < 1 || value > 60000000)
+            return set_err(c, GS_EINVAL, "wait limit %d us not in 1..60000000", value);
+        c->wait_ns = (unsigned long long)value * 1000ull;
+        return GS_OK;
+    }
     return set_err(c, GS_EINVAL, "unknown option %d", option);
 }
 
@@ -222,7 +231,35 @@ gs_status gs_get_option(gs_ctx* c, int option, int* value) {
         *value = c->opt_multi_batch;
         return GS_OK;
     }
+    if (option == GS_OPT_WAIT_LIMIT_US) {
+        *value = (int)(c->wait_ns / 1000ull);
+        return GS_OK;
+    }
     return set_err(c, GS_EINVAL, "unknown option %d", option);
+}
+
+gs_status gs_selftest_wait(gs_ctx* c, int which) {
+    if (check_ctx(c) != GS_OK) return GS_EINVAL;
+    gs_status got = GS_OK;
+    if (which == 0) {
+        gs_status s = selftest_grid_timeout(c, &got);
+        if (s != GS_OK) return s;
+    } else if (which == 1) {
+        int* err_dev = (int*)(c->scal_dev + 32);
+        GS_CUDA(c, cudaMemsetAsync(err_dev, 0, sizeof(int), c->stream));
+        gs_status s = selftest_mbar_timeout(c, err_dev);
+        if (s != GS_OK) return s;
+        int h = 0;
+        GS_CUDA(c, cudaMemcpyAsync(&h, err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        got = (gs_status)h;
+    } else {
+        return set_err(c, GS_EINVAL, "unknown self-test %d", which);
+    }
+    if (got == GS_TIMEOUT)
+        return set_err(c, GS_TIMEOUT, "%s wait ran out after %.3f ms, as the self-test intends",
+                       which == 0 ? "grid-barrier" : "mbarrier", 1e-6 * (double)c->wait_ns);
+    return set_err(c, got, "the self-test's wait did not run out (status %d)", (int)got);
 }
 
 gs_status gs_set_gauge(gs_ctx* c, const void* U_dev) {

@@ -12,6 +12,7 @@ struct GridSync {
     unsigned int* count;  // arrivals since the launch began
     unsigned int* gen;    // unused (kept zero)
     int* err;             // GS_TIMEOUT once any block gave up
+    unsigned long long wait_ns;  // bound on one wait (0: kWaitNs)
 };
 
 __device__ __forceinline__ unsigned int vload(const unsigned int* p) {
@@ -32,8 +33,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // is (no block can arrive at barrier k + 1 before every block has arrived at
 // barrier k), so the block waits, with acquire loads, for the count of that
 // barrier's last arrival.  A waiting block gives up after kSpinLimit polls or
-// kWaitNs of global time, whichever comes first, and records GS_TIMEOUT; a
-// block that sees the error word set leaves as well.
+// g.wait_ns of global time (the context's wait limit; kWaitNs if 0),
+// whichever comes first, and records GS_TIMEOUT; a block that sees the error
+// word set leaves as well.
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 __device__ bool grid_sync(const GridSync& g) {
     __shared__ int s_ok;
@@ -45,6 +47,7 @@ __device__ bool grid_sync(const GridSync& g) {
         unsigned int old;
         asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(g.count) : "memory");
         const unsigned int target = (old / nb + 1u) * nb;
+        const unsigned long long limit = g.wait_ns ? g.wait_ns : kWaitNs;
         long long spins = 0;
         const unsigned long long t0 = global_ns();
         for (;;) {
@@ -55,7 +58,7 @@ __device__ bool grid_sync(const GridSync& g) {
                 ok = 0;
                 break;
             }
-            if (++spins > kSpinLimit || global_ns() - t0 > kWaitNs) {
+            if (++spins > kSpinLimit || global_ns() - t0 > limit) {
                 atomicExch(g.err, (int)GS_TIMEOUT);
                 ok = 0;
                 break;

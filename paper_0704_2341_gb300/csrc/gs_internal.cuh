@@ -203,6 +203,7 @@ struct gs_ctx {
     int opt_inner_kernel = 0;          // 0 = persistent cooperative BiCGStab, 1 = one launch per phase
     int opt_net_kernel = 0;            // 0 = tensor-core network kernels (C = 24), 1 = CUDA cores only
     int opt_multi_batch = 0;           // 0 = by rest-set size, 1 = sources together, 2 = one at a time
+    unsigned long long wait_ns = 1000000000ull;  // bound on every device-side wait (GS_OPT_WAIT_LIMIT_US)
     void* persist = nullptr;           // persistent-solver scratch (persistent.cu)
     void* multi = nullptr;             // multi-RHS workspaces (multi.cu)
     int coop_block_cap = 0;            // cap on cooperative grids (0 = whole GPU; batched solves)
@@ -343,5 +344,10 @@ gs_status outer_solve(gs_ctx* c, const Plan* p, const double2* wb, double2* xb,
                       const gs_solve_opts& o, gs_solve_stats& st);
 
 int grid_for(int64_t n, int block, int max_blocks);
+
+// failure-detection self-tests (persistent.cu, net_tc.cu): a bounded wait made
+// to run out on purpose
+gs_status selftest_grid_timeout(gs_ctx* c, gs_status* result);
+gs_status selftest_mbar_timeout(gs_ctx* c, int* err_dev);
 
 }  // namespace gs

@@ -360,6 +360,8 @@ struct MixedState {
     std::vector<LpPlanData> plans;
     double2* e64 = nullptr;  // FP64 correction of the fallback solve (rest set)
     int64_t e64_cap = 0;
+    double2* zbak = nullptr; // z before a low-precision cycle's correction (restored if it fails)
+    int64_t zbak_cap = 0;
 };
 
 static MixedState* mixed_of(gs_ctx* c) {
@@ -377,6 +379,7 @@ void free_mixed(gs_ctx* c) {
     cudaFree(m->w.counter);
     cudaFree(m->w.rr64);
     cudaFree(m->e64);
+    cudaFree(m->zbak);
     if (m->w.rr64_host) cudaFreeHost(m->w.rr64_host);
     for (auto& pd : m->plans) {
         cudaFree(pd.nbr_r);
@@ -646,6 +649,19 @@ gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2*
     ra.plan = p;
     ra.nbr = p->nbr;
     ra.links = p->links;
+    if (m->zbak_cap < n) {
+        cudaFree(m->zbak);
+        m->zbak = nullptr;
+        if (cudaMalloc(&m->zbak, vbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, GS_ENOMEM, "allocating the correction backup failed");
+        }
+        m->zbak_cap = n;
+    }
+    // A low-precision cycle that fails (a zero or non-finite scalar, e.g. a
+    // network whose output is not finite) or whose correction leaves a
+    // non-finite residual is discarded: z and r keep their values from before
+    // the cycle and the plain FP64 BiCGStab below finishes the solve.
     int cycles = 0;
     for (; cycles < 100 && rr > target; ++cycles) {
         if (stalls >= 2) break;
@@ -663,6 +679,10 @@ gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2*
                 m->e64_cap = n;
             }
             s = inner_fgmres_net(c, p, r64, m->e64, lo_tol, o.inner_restart, &it);
+            if (s == GS_NONFINITE || s == GS_BREAKDOWN) {
+                iters_total += it;
+                break;
+            }
         } else if (c->opt_inner_kernel == 0) {
             // init + all iterations of the cycle in one cooperative launch
             LpArgs A;
@@ -723,6 +743,7 @@ gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2*
         }
         if (s != GS_OK) return s;
         iters_total += it;
+        GS_CUDA(c, cudaMemcpyAsync(m->zbak, z, vbytes, cudaMemcpyDeviceToDevice, c->stream));
         // z += ||r|| e ; r = t - D_rr z (FP64) ; ||r||^2
         if (o.inner_solver == GS_INNER_FGMRES_NET) {
             if ((s = launch_axpby(c, make_double2(1.0, 0.0), m->e64, make_double2(1.0, 0.0), z,
@@ -742,7 +763,13 @@ gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2*
                                    c->stream));
         GS_CUDA(c, cudaStreamSynchronize(c->stream));
         const double rr_new = *w.rr64_host;
-        if (!isfinite(rr_new)) return set_err(c, GS_NONFINITE, "non-finite mixed residual");
+        if (!isfinite(rr_new)) {
+            // discard the cycle: z back to its previous value, r recomputed
+            // from it (the same deterministic stencil, so rr is unchanged)
+            GS_CUDA(c, cudaMemcpyAsync(z, m->zbak, vbytes, cudaMemcpyDeviceToDevice, c->stream));
+            if ((s = launch_stencil_f64(c, ra)) != GS_OK) return s;
+            break;
+        }
         stalls = (rr_new > 0.25 * rr) ? stalls + 1 : 0;
         rr = rr_new;
     }

@@ -740,6 +740,7 @@ static gs_status inner_solve_multi(gs_ctx* c, const Plan* p, int N, const double
         P.sync.count = m->words;
         P.sync.gen = m->words + 1;
         P.sync.err = (int*)(m->words + 2);
+        P.sync.wait_ns = c->wait_ns;
         P.st = m->st;
         void* args[] = {&P};
         GS_CUDA(c, cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)g), dim3(N, SB), args,

@@ -21,7 +21,8 @@
 // into the A stage (double-buffered, reused once the tensor core has
 // committed the chunk two back; a thread handles two input rows of one site); one thread moves B_j by a bulk copy and,
 // after the block barrier, issues the chunk's six MMAs and commits them to
-// the stage's mbarrier.  Every wait is bounded (1 s of global time); on a
+// the stage's mbarrier.  Every wait is bounded (the context's wait limit,
+// GS_OPT_WAIT_LIMIT_US, 1 s by default); on a
 // timeout the kernel stops, frees its tensor memory and raises err.
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -77,12 +78,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait: true when the phase of the given parity has completed
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// bounded wait: true when the phase of the given parity has completed, false
+// after wait_ns of global time (the context's wait limit) or 2^30 polls
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long wait_ns) {
     const uint64_t t0 = gtime();
     for (uint32_t it = 0; it < (1u << 30); ++it) {
         if (mbar_try(bar, parity)) return true;
-        if ((it & 255u) == 255u && gtime() - t0 > 1000000000ull) return false;
+        if ((it & 255u) == 255u && gtime() - t0 > wait_ns) return false;
     }
     return false;
 }
@@ -183,7 +185,7 @@ __device__ __forceinline__ void stage_chunk(const unsigned char* P, const float2
 __global__ void __launch_bounds__(kThreads, 1)
     k_net_conv_tc(const __nv_bfloat162* __restrict__ in, float2* __restrict__ out,
                   const __nv_bfloat16* __restrict__ Bw, const float2* __restrict__ U32,
-                  const int2* __restrict__ nbr, int64_t V, int* err) {
+                  const int2* __restrict__ nbr, int64_t V, int* err, unsigned long long wait_ns) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     __shared__ __align__(8) uint64_t bfull[2], mdone[2];
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             __syncthreads();
             const uint32_t s = g & 1u, u = g >> 1;
-            if (g >= 2 && !mbar_wait(su32(&mdone[s]), (u - 1) & 1u)) bad = 1;
+            if (g >= 2 && !mbar_wait(su32(&mdone[s]), (u - 1) & 1u, wait_ns)) bad = 1;
             if (tid == 0 && !bad) {
                 const uint32_t bar = su32(&bfull[s]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBBytes)
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             if (tid == 0) {
-                if (!mbar_wait(su32(&bfull[s]), u & 1u)) {
+                if (!mbar_wait(su32(&bfull[s]), u & 1u, wait_ns)) {
                     bad = 1;
                 } else {
                     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // epilogue: the last chunk's commit covers every MMA of the tile
         {
             const uint32_t gl = g - 1, s = gl & 1u, u = gl >> 1;
-            if (!mbar_wait(su32(&mdone[s]), u & 1u)) bad = 1;
+            if (!mbar_wait(su32(&mdone[s]), u & 1u, wait_ns)) bad = 1;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!bad) {
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // timeout give the in-flight ones a bounded time before freeing
     if (bad && tid == 0 && g > 0) {
         const uint32_t gl = g - 1;
-        mbar_wait(su32(&mdone[gl & 1u]), (gl >> 1) & 1u);
+        mbar_wait(su32(&mdone[gl & 1u]), (gl >> 1) & 1u, wait_ns);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -387,7 +389,7 @@ __device__ __forceinline__ uint64_t phi_desc(uint32_t addr) {
 
 __global__ void __launch_bounds__(kPhiThreads, 2)
     k_net_phi_tc(const float2* __restrict__ in, float2* __restrict__ phi, const __nv_bfloat16* __restrict__ Bw,
-                 int64_t V, int* err) {
+                 int64_t V, int* err, unsigned long long wait_ns) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     unsigned char* sA = base;
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(kPhiThreads, 2)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
-            if ((used == 0 && !mbar_wait(su32(&bfull), 0u))) {
+            if ((used == 0 && !mbar_wait(su32(&bfull), 0u, wait_ns))) {
                 bad = 1;
             } else {
                 asm volatile("tcgen05.fence::after_thread_sync;");
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(kPhiThreads, 2)
             break;
         }
         ++used;
-        if (!mbar_wait(su32(&mdone), (used - 1) & 1u)) bad = 1;
+        if (!mbar_wait(su32(&mdone), (used - 1) & 1u, wait_ns)) bad = 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!__syncthreads_or(bad)) {
             // warp w: lanes 32 (w % 4) .. + 31, columns 40 (w / 4) .. + 39
@@ -514,7 +516,7 @@ __global__ void __launch_bounds__(kPhiThreads, 2)
     }
     if (bad && tid == 0) atomicExch(err, 1);
     // the weight copy must have landed before the CTA exits
-    if (tid == 0 && used == 0) mbar_wait(su32(&bfull), 0u);
+    if (tid == 0 && used == 0) mbar_wait(su32(&bfull), 0u, wait_ns);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -565,7 +567,8 @@ __device__ __forceinline__ uint64_t l1_desc(uint32_t addr) {
 
 __global__ void __launch_bounds__(kL1Threads, 2)
     k_net_l1_tc(const float2* __restrict__ in, __nv_bfloat162* __restrict__ out, const __nv_bfloat16* __restrict__ Bw,
-                const float2* __restrict__ U32, const int2* __restrict__ nbr, int64_t V, int* err) {
+                const float2* __restrict__ U32, const int2* __restrict__ nbr, int64_t V, int* err,
+                unsigned long long wait_ns) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     unsigned char* sA = base;
@@ -668,7 +671,7 @@ __global__ void __launch_bounds__(kL1Threads, 2)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
-            if (used == 0 && !mbar_wait(su32(&bfull), 0u)) {
+            if (used == 0 && !mbar_wait(su32(&bfull), 0u, wait_ns)) {
                 bad = 1;
             } else {
                 asm volatile("tcgen05.fence::after_thread_sync;");
@@ -693,7 +696,7 @@ __global__ void __launch_bounds__(kL1Threads, 2)
             break;
         }
         ++used;
-        if (!mbar_wait(su32(&mdone), (used - 1) & 1u)) bad = 1;
+        if (!mbar_wait(su32(&mdone), (used - 1) & 1u, wait_ns)) bad = 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!__syncthreads_or(bad)) {
             // warp w: lanes 32 (w % 4) .. + 31, columns 96 (w / 4) .. + 95
@@ -731,7 +734,7 @@ __global__ void __launch_bounds__(kL1Threads, 2)
         }
     }
     if (bad && tid == 0) atomicExch(err, 1);
-    if (tid == 0 && used == 0) mbar_wait(su32(&bfull), 0u);
+    if (tid == 0 && used == 0) mbar_wait(su32(&bfull), 0u, wait_ns);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -751,6 +754,19 @@ __global__ void k_net_l1_pack(const float2* __restrict__ WT, __nv_bfloat16* __re
             v = cout == 0 ? (cin == 0 ? w.x : -w.y) : (cin == 0 ? w.y : w.x);
         }
         Bw[l1_off(np, kp) / 2] = __float2bfloat16_rn(v);
+    }
+}
+
+// Failure-detection self-test: one thread waits, through the same bounded
+// mbar_wait as the kernels above, on an mbarrier that nothing ever arrives
+// at; the wait runs out after wait_ns and the kernel records GS_TIMEOUT.
+__global__ void k_selftest_mbar_timeout(int* err, unsigned long long wait_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        if (!mbar_wait(su32(&bar), 0u, wait_ns)) atomicExch(err, (int)GS_TIMEOUT);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(su32(&bar)));
     }
 }
 
@@ -781,7 +797,7 @@ gs_status net_l1_tc(gs_ctx* c, const float2* in, __nv_bfloat162* out, const __nv
     const int64_t ntiles = (3 * V + kL1Rows - 1) / kL1Rows;
     const int64_t cap = 2LL * c->num_sms;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    k_net_l1_tc<<<grid, kL1Threads, kL1Smem, c->stream>>>(in, out, Bw, U32, nbr, V, err);
+    k_net_l1_tc<<<grid, kL1Threads, kL1Smem, c->stream>>>(in, out, Bw, U32, nbr, V, err, c->wait_ns);
     c->launches++;
     GS_CHECK_LAUNCH(c);
     return GS_OK;
@@ -799,7 +815,7 @@ gs_status net_phi_tc(gs_ctx* c, const float2* in, float2* phi, const __nv_bfloat
     const int64_t ntiles = (3 * V + kPhiRows - 1) / kPhiRows;
     const int64_t cap = 2LL * c->num_sms;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    k_net_phi_tc<<<grid, kPhiThreads, kPhiSmem, c->stream>>>(in, phi, Bw, V, err);
+    k_net_phi_tc<<<grid, kPhiThreads, kPhiSmem, c->stream>>>(in, phi, Bw, V, err, c->wait_ns);
     c->launches++;
     GS_CHECK_LAUNCH(c);
     return GS_OK;
@@ -810,7 +826,15 @@ gs_status net_conv_tc(gs_ctx* c, const __nv_bfloat162* in, float2* out, const __
     GS_CUDA(c, cudaFuncSetAttribute(k_net_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     const int64_t ntiles = (3 * V + kRows - 1) / kRows;
     const int grid = (int)(ntiles < c->num_sms ? ntiles : c->num_sms);
-    k_net_conv_tc<<<grid, kThreads, kSmem, c->stream>>>(in, out, Bw, U32, nbr, V, err);
+    k_net_conv_tc<<<grid, kThreads, kSmem, c->stream>>>(in, out, Bw, U32, nbr, V, err, c->wait_ns);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    return GS_OK;
+}
+
+// Runs k_selftest_mbar_timeout; *err_dev receives GS_TIMEOUT when the wait ran out.
+gs_status selftest_mbar_timeout(gs_ctx* c, int* err_dev) {
+    k_selftest_mbar_timeout<<<1, 32, 0, c->stream>>>(err_dev, c->wait_ns);
     c->launches++;
     GS_CHECK_LAUNCH(c);
     return GS_OK;

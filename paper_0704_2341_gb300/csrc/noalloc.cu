@@ -3,8 +3,6 @@
 // the two tables that kernel reads besides its inputs and outputs -- the
 // neighbour table and the packed (-1/2 U) links -- live in one file-scope
 // device array instead of context-owned allocations.
-#include <mutex>
-
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -20,28 +18,19 @@ constexpr size_t kScratchBytes = kNbrBytes + kLinkBytes;
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (the first call on a device does this set-up).
+// Device address of the scratch array in the current device's context.  The
+// first call on a device loads the library's module there (the set-up, which
+// is why that first call must come before any stream capture); after that the
+// lookup is a cheap query.  It is made on every call, so a device that was
+// reset, or a primary context destroyed and created again (the module then
+// reloads, possibly at another address), never sees a stale pointer.
 gs_status scratch_address(void** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
         cudaGetLastError();
         return GS_ECUDA;
     }
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (g_scratch_addr[dev] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
-            return GS_ECUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return GS_OK;
 }
 
@@ -82,12 +71,15 @@ using namespace gs;
 extern "C" gs_status wilson_apply_noalloc(const int dims[4], double m0, const void* U_dev,
                                           const void* x_dev, void* y_dev, void* stream) {
     if (!dims || !U_dev || !x_dev || !y_dev || !isfinite(m0)) return GS_EINVAL;
+    for (int mu = 0; mu < 4; ++mu)
+        if (dims[mu] < 2) return GS_EINVAL;
+    // every factor is checked against the bound before it multiplies V, so the
+    // product never overflows whatever the extents
     int64_t V = 1;
     for (int mu = 0; mu < 4; ++mu) {
-        if (dims[mu] < 2) return GS_EINVAL;
+        if (dims[mu] > kNoAllocMaxSites / V) return GS_ETOOLARGE;
         V *= dims[mu];
     }
-    if (V > kNoAllocMaxSites) return GS_ETOOLARGE;
     void* base = nullptr;
     gs_status s = scratch_address(&base);
     if (s != GS_OK) return s;

@@ -613,6 +613,21 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_lp(PArgsLp P) {
     }
 }
 
+// Failure-detection self-test: block 0 never arrives at the grid barrier (it
+// waits, bounded by the same limit, on a flag that nothing sets); every other
+// block's grid_sync runs out of time and records GS_TIMEOUT in the error word.
+__global__ void __launch_bounds__(kPThreads) k_selftest_grid_timeout(GridSync g, const int* never) {
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) {
+            const unsigned long long t0 = global_ns();
+            while (vload(never) == 0 && global_ns() - t0 < g.wait_ns) {
+            }
+        }
+        return;
+    }
+    grid_sync(g);
+}
+
 // co-resident grid for a cooperative launch: at most `want` blocks
 template <class K>
 static int coop_grid(gs_ctx* c, K kernel, int64_t want) {
@@ -696,6 +711,7 @@ gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs
     P.sync.count = ps->words;
     P.sync.gen = ps->words + 1;
     P.sync.err = (int*)(ps->words + 2);
+    P.sync.wait_ns = c->wait_ns;
     P.st = w.st;
     P.phases = c->prof.on ? c->prof.phases_dev : nullptr;
     void* args[] = {&P};
@@ -739,6 +755,7 @@ static gs_status persistent_bicg_lp_t(gs_ctx* c, const LpArgs& A, const LpArgs& 
     P.sync.count = ps->words;
     P.sync.gen = ps->words + 1;
     P.sync.err = (int*)(ps->words + 2);
+    P.sync.wait_ns = c->wait_ns;
     P.st = st;
     void* args[] = {&P};
     GS_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_bicg_persistent_lp<S>, dim3(g),
@@ -753,6 +770,30 @@ gs_status persistent_bicg_lp(gs_ctx* c, int prec, const LpArgs& A, const LpArgs&
     if (prec == GS_BF16)
         return persistent_bicg_lp_t<__nv_bfloat16>(c, A, C, r64, rr64, vecs, st, n, tol, maxit);
     return persistent_bicg_lp_t<float>(c, A, C, r64, rr64, vecs, st, n, tol, maxit);
+}
+
+// Runs k_selftest_grid_timeout on a co-resident grid of two blocks with the
+// persistent solvers' barrier words; returns the error word's status.
+gs_status selftest_grid_timeout(gs_ctx* c, gs_status* result) {
+    PersistScratch* ps = nullptr;
+    gs_status s = persist_scratch(c, &ps);
+    if (s != GS_OK) return s;
+    GS_CUDA(c, cudaMemsetAsync(ps->words, 0, 4 * sizeof(unsigned int), c->stream));
+    GridSync g;
+    g.count = ps->words;
+    g.gen = ps->words + 1;
+    g.err = (int*)(ps->words + 2);
+    g.wait_ns = c->wait_ns;
+    const int* never = (const int*)(ps->words + 3);   // zeroed above, never written
+    void* args[] = {&g, &never};
+    GS_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_selftest_grid_timeout, dim3(2),
+                                           dim3(kPThreads), args, 0, c->stream));
+    c->launches++;
+    int h = 0;
+    GS_CUDA(c, cudaMemcpyAsync(&h, ps->words + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    *result = (gs_status)h;
+    return GS_OK;
 }
 
 }  // namespace gs

@@ -196,6 +196,52 @@ using namespace gs;
 
 extern "C" {
 
+gs_status schur_apply_approx(gs_ctx* c, int type, int dir, int inverse, int order, const void* xb_dev,
+                             void* yb_dev) {
+    if (!c) return GS_EINVAL;
+    if (order == 2) return schur_apply_reusken(c, type, dir, inverse, xb_dev, yb_dev);
+    if (order != 1) return set_err(c, GS_EINVAL, "approximation order %d is not 1 or 2", order);
+    if (!xb_dev || !yb_dev) return set_err(c, GS_EINVAL, "null vector");
+    if (type != GS_TYPE_I && type != GS_TYPE_II) return set_err(c, GS_EINVAL, "unknown permutation type %d", type);
+    if (!c->have_gauge) return set_err(c, GS_ENOGAUGE, "no gauge field set");
+    Plan* p = nullptr;
+    gs_status s = get_plan(c, type, dir, inverse, &p);
+    if (s != GS_OK) return s;
+    const int64_t nb = p->nb, V = c->V, nr = V - nb;
+    if ((s = ensure_inner(c, nr)) != GS_OK) return s;
+    double2* t = c->inner.rhs;
+    double2* z = c->inner.sol;
+    const double2* xb = (const double2*)xb_dev;
+    // first order: D_rr replaced by its diagonal d = (m0 + 4) 1, so with
+    // t = -D_rb x_b, z = t / (m0 + 4) and S~_bb x_b = (D [x_b; z])_b
+    StencilArgs a;
+    memset(&a, 0, sizeof a);
+    a.diag = c->m0 + 4.0;
+    a.plan = p;
+    a.nbr = p->nbr;
+    a.links = p->links;
+    a.out = t;
+    a.o0 = nb;
+    a.n_out = nr;
+    a.inA = xb;
+    a.a0 = 0;
+    a.a1 = nb;
+    a.b1 = nb;
+    a.negate = 1;
+    if ((s = launch_stencil_f64(c, a)) != GS_OK) return s;
+    if ((s = launch_scale_copy(c, t, z, nr * kSiteC, 1.0 / (c->m0 + 4.0))) != GS_OK) return s;
+    a.out = (double2*)yb_dev;
+    a.o0 = 0;
+    a.n_out = nb;
+    a.inA = xb;
+    a.a0 = 0;
+    a.a1 = nb;
+    a.inB = z;
+    a.b1 = V;
+    a.negate = 0;
+    return launch_stencil_f64(c, a);
+}
+
 gs_status schur_apply_reusken(gs_ctx* c, int type, int dir, int inverse, const void* xb_dev, void* yb_dev) {
     if (!c) return GS_EINVAL;
     if (!xb_dev || !yb_dev) return set_err(c, GS_EINVAL, "null vector");

@@ -26,3 +26,17 @@ def rel(a, b):
     b = np.asarray(b).ravel()
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def maxrel(a, b):
+    """Element-wise error: max_i |a_i - b_i| / max_i |b_i| (a component that
+    is wrong by more than the tolerance fails it, however small the others)."""
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    mb = np.abs(b).max() if b.size else 0.0
+    return np.abs(a - b).max() / (mb if mb > 0 else 1.0) if a.size else 0.0
+
+
+def close(a, b, tol):
+    """Both the norm-wise and the element-wise relative error within tol."""
+    return rel(a, b) <= tol and maxrel(a, b) <= tol

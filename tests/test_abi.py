@@ -107,4 +107,12 @@ def test_argument_checks_come_before_any_cuda_call():
     assert gs.wilson_apply_noalloc((4, 4, 4, 4), float("inf"), fake, fake, fake) == gs.GS_EINVAL
     assert gs.wilson_apply_noalloc((16, 16, 16, 16), 0.1, fake, fake, fake) == \
         gs._binding.GS_ETOOLARGE
+    # extents whose product overflows 64 bits: each factor is bounded before
+    # it multiplies, so the library (called directly, past the binding's own
+    # check) still refuses them
+    big = (ct.c_int * 4)(*([2 ** 31 - 1] * 4))
+    assert lib.wilson_apply_noalloc(big, ct.c_double(0.1), fake, fake, fake, None) == \
+        gs._binding.GS_ETOOLARGE
+    assert create((2 ** 31 - 1,) * 4, 0.1) == gs.GS_EINVAL
+    assert create((2 ** 16, 2 ** 16, 2 ** 16, 2 ** 16), 0.1) == gs.GS_EINVAL
     assert gs.gs_last_error(None) == "null context"

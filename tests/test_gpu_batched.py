@@ -7,7 +7,7 @@ import scipy.sparse.linalg as sla
 
 import lattice_inputs as li
 from oracle import dirac, permute, schur
-from tests.gpu_util import lib, rel, to_dev, torch_cuda
+from tests.gpu_util import close, lib, maxrel, rel, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -74,7 +74,7 @@ def test_schur_solve_multi_matches_direct(env, prec, t, mu, inv):
     x = xd.cpu().numpy().reshape(N, -1)
     for j in range(N):
         xs = sla.spsolve(D, f[j].ravel())
-        assert rel(x[j], xs) <= 1e-9
+        assert close(x[j], xs, 1e-9)
     assert st.true_residual <= 1e-10
     ctx.close()
 
@@ -122,7 +122,7 @@ def test_schur_solve_batched_concurrent_problems(env):
     for (D, f), pr, st in zip(refs, probs, stats):
         x = pr["x"].cpu().numpy().reshape(pr["nrhs"], -1)
         for j in range(pr["nrhs"]):
-            assert rel(x[j], sla.spsolve(D, f[j].ravel())) <= 1e-9
+            assert close(x[j], sla.spsolve(D, f[j].ravel()), 1e-9)
         assert st.true_residual <= 1e-10
     for c in ctxs:
         c.close()
@@ -158,7 +158,7 @@ def test_batch_shape_option_gives_the_same_solutions(env):
         st = ctx.schur_solve_multi(1, 0, 0, 3, f, x, o)
         assert st.true_residual <= 1e-10
         xs.append(x.cpu().numpy())
-    assert rel(xs[0], xs[1]) <= 1e-8
+    assert close(xs[0], xs[1], 1e-8)
     with pytest.raises(gs.GschurError):
         ctx.set_option(gs.GS_OPT_MULTI_BATCH, 3)
     ctx.close()

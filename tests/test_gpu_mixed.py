@@ -10,7 +10,7 @@ import scipy.sparse.linalg as sla
 
 import lattice_inputs as li
 from oracle import dirac, permute, schur
-from tests.gpu_util import lib, rel, to_dev, torch_cuda
+from tests.gpu_util import close, lib, maxrel, rel, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 TYPES = [(1, 0, False), (2, 0, False), (1, 0, True), (2, 0, True)]
@@ -45,7 +45,7 @@ def test_mixed_schur_apply_matches_oracle(env, prec, t, mu, inv, kernel):
     st = ctx.schur_apply(t, mu, int(inv), xbd, ybd,
                          gs.gs_default_opts(inner_prec=p, inner_tol=1e-13))
     ref = schur.SchurOperator(dirac.wilson_matrix(U, dims, m0), perm, nb, inner="direct")(xb)
-    assert rel(ybd.cpu().numpy(), ref) <= 1e-11
+    assert close(ybd.cpu().numpy(), ref, 1e-11)
     assert st.lowp_cycles >= 2 and st.inner_residual <= 1e-13
     ctx.close()
 
@@ -64,7 +64,7 @@ def test_mixed_schur_solve_ragged_and_direct(env, prec):
     p = gs.GS_F32 if prec == "f32" else gs.GS_BF16
     for t, mu, inv in TYPES:
         st = ctx.schur_solve(t, mu, int(inv), fd, xd, gs.gs_default_opts(inner_prec=p))
-        assert rel(xd.cpu().numpy(), xs) <= 1e-9
+        assert close(xd.cpu().numpy(), xs, 1e-9)
         assert st.true_residual <= 1e-10
     ctx.close()
 

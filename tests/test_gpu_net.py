@@ -7,7 +7,7 @@ import scipy.sparse.linalg as sla
 
 import lattice_inputs as li
 from oracle import dirac, net as onet, permute
-from tests.gpu_util import lib, rel, to_dev, torch_cuda
+from tests.gpu_util import close, lib, maxrel, rel, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -58,13 +58,14 @@ def test_forward_backward_match_oracle(env, C):
     assert abs(loss - L) <= 1e-4 * L
     for l in range(3):
         g = nt.get(1, l).astype(np.complex128)
-        assert rel(g, G[l]) <= 1e-4, l
+        assert close(g, G[l], 1e-4), l
     # inference (BF16 weights) against the oracle output
     t64 = to_dev(t.astype(np.complex128), torch)
     y64 = torch.empty_like(t64)
     nt.apply(ctx.handle, 1, 0, 0, t64, y64)
     torch.cuda.synchronize()
-    assert rel(y64.cpu().numpy(), y[perm[nb:]]) <= 3e-2
+    got = y64.cpu().numpy()
+    assert rel(got, y[perm[nb:]]) <= 3e-2 and maxrel(got, y[perm[nb:]]) <= 2 * 3e-2
     nt.close()
     ctx.close()
 
@@ -96,7 +97,7 @@ def test_training_reduces_loss_and_fgmres_net_solves(env):
     xd = torch.empty_like(fd)
     st = ctx.schur_solve(1, 0, 0, fd, xd, learned.fgmres_net_opts())
     xs = sla.spsolve(dirac.wilson_matrix(U, dims, m0).tocsc(), f.ravel())
-    assert rel(xd.cpu().numpy(), xs) <= 1e-9
+    assert close(xd.cpu().numpy(), xs, 1e-9)
     assert st.true_residual <= 1e-10
     ctx.set_net(None)
     nt.close()
@@ -146,7 +147,7 @@ def test_learned_gain_over_the_method_without_it(env):
     st_id = ctx.solve_rr(1, 0, 0, t, z_id, learned.fgmres_net_opts(inner_tol=1e-8, lowp_tol=1e-8,
                                                                     inner_restart=64))
     ctx.set_net(None)
-    assert rel(z_net.cpu().numpy(), z_plain.cpu().numpy()) <= 1e-6
+    assert close(z_net.cpu().numpy(), z_plain.cpu().numpy(), 1e-6)
     assert st_net.inner_iters < st_id.inner_iters
     assert st_net.inner_iters < 2 * st_plain.inner_iters   # D_rr applications: 1 vs 2 per step
     print("\nlearned gain on 8^4: FGMRES+trained net %d steps, FGMRES+untrained %d, "
@@ -189,13 +190,13 @@ def test_tensor_core_layer_matches_cuda_cores_and_oracle(env, dims):
     y_tc, y_cc = y_tc.cpu().numpy(), y_cc.cpu().numpy()
     assert np.isfinite(y_tc).all()
     # BF16 rounding of the transported activations only: ~1e-3 relative
-    assert rel(y_tc, y_cc) <= 5e-3
+    assert rel(y_tc, y_cc) <= 5e-3 and maxrel(y_tc, y_cc) <= 2 * 5e-3
     tfull = np.zeros((V, 12), complex)
     tfull[perm[nb:]] = t
     y = onet.forward([w.astype(np.complex128) for w in Ws], tfull.reshape(V, 4, 3),
                      onet.transports(U, dims))[-1].reshape(V, 12)[perm[nb:]]
-    assert rel(y_tc, y) <= 1e-2
-    assert rel(y_cc, y) <= 1e-2
+    assert rel(y_tc, y) <= 1e-2 and maxrel(y_tc, y) <= 2 * 1e-2
+    assert rel(y_cc, y) <= 1e-2 and maxrel(y_cc, y) <= 2 * 1e-2
     # repeated application is deterministic
     y2 = torch.empty_like(td)
     nt.apply(ctx.handle, 1, 0, 0, td, y2)

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import lattice_inputs as li
+from oracle import dirac
 from tests.gpu_util import lib, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
@@ -36,6 +37,9 @@ def test_noalloc_matches_wilson_apply_on_two_calls_in_a_row():
         torch.cuda.synchronize()
         a, b = y.cpu().numpy(), y_ref.cpu().numpy()
         assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+        # and directly against the oracle's assembled D, element by element
+        ref = dirac.wilson_matrix(U.cpu().numpy(), dims, m0) @ x.cpu().numpy().ravel()
+        assert np.abs(a.ravel() - ref).max() <= 1e-13 * np.abs(ref).max()
         ctx.close()
 
 
@@ -46,3 +50,19 @@ def test_noalloc_rejects_lattices_beyond_its_scratch():
     z = torch.zeros(1, dtype=torch.complex128, device="cuda:0")
     assert gs.wilson_apply_noalloc(dims, 0.1, z, z, z, None) == gs.GS_ETOOLARGE
     assert gs.wilson_apply_noalloc((1, 8, 8, 8), 0.1, z, z, z, None) == gs.GS_EINVAL
+
+
+def test_noalloc_refuses_undersized_or_mistyped_buffers():
+    """The binding checks the buffer sizes and types the lattice needs before
+    any pointer reaches the library (the library itself cannot see them)."""
+    torch = torch_cuda()
+    gs = lib()
+    dims = (8, 8, 8, 8)
+    V = li.volume(dims)
+    U = torch.zeros(V * 36, dtype=torch.complex128, device="cuda:0")
+    x = torch.zeros(V * 12, dtype=torch.complex128, device="cuda:0")
+    for args in ((U[:-1], x, x.clone()), (U, x[:V], x.clone()), (U, x, x[:-12]),
+                 (U, x.to(torch.complex64), x.clone())):
+        with pytest.raises(gs.GschurError) as e:
+            gs.wilson_apply_noalloc(dims, 0.1, *args)
+        assert e.value.status == gs.GS_EINVAL
