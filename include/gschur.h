@@ -418,6 +418,61 @@ gs_status gs_net_train_step(gs_ctx* ctx, gs_net* net, int type, int dir, int inv
 /* Attach (or with NULL detach) the network used by GS_INNER_FGMRES_NET. */
 gs_status gs_set_net(gs_ctx* ctx, gs_net* net);
 
+/* The cyclic-reduction V-cycle preconditioner of Section 4 (the "3-level
+ * V-cycle" of Table 1 is nsteps = 2).  Level 0 is D on the context's
+ * lattice; level l + 1 is the Section 3 approximation S~ (order 2; order 1:
+ * D_rr's couplings ignored) of level l's operator on its coarse set, indexed
+ * by level l's coarse labels in order; coarsening step l uses the
+ * permutation type[l], dir[l] (Type II only), inverse[l], applied at levels
+ * >= 1 to the coarse labels as a lattice of the coarse extents (Type I halves
+ * every extent, Type II(dir) halves L_dir; the blocked extents must be
+ * even).  The coarsest level (at most 1024 sites) is inverted exactly (a
+ * dense inverse); every rest-set inverse A_rr^-1 is BiCGStab to rest_tol
+ * (the paper: 1e-2), at most rest_max_iter steps (the last iterate is used
+ * beyond).  One application x = V(f) is the block UL solve of Section 1 with
+ * the Schur complement replaced by the next level:
+ *   w_b = F_b - A_br A_rr^-1 F_r,  x_b = V_next(w_b),  x_r = A_rr^-1 (F_r - A_rb x_b).
+ * The lower levels' operators are assembled once, here: S~ is applied to
+ * probe vectors (one per colour of a column colouring of its pattern and
+ * spin-colour component) and the results fill a block-sparse matrix.  The V-cycle belongs to the context and
+ * must be destroyed before it; a new gauge field needs a new V-cycle.
+ * Synchronises the stream. */
+typedef struct gs_vcycle gs_vcycle;
+gs_status gs_vcycle_create(gs_ctx* ctx, int nsteps, const int* type, const int* dir,
+                           const int* inverse, int order, double rest_tol, int rest_max_iter,
+                           gs_vcycle** vc_out);
+gs_status gs_vcycle_destroy(gs_vcycle* vc);
+/* x = V(f): f_dev, x_dev complex128 [V][4][3], site order, not overlapping.
+ * stats (may be NULL): inner_solves / inner_iters / inner_max_seen count the
+ * rest-set BiCGStab solves of all levels, lowp_fallbacks those stopped at
+ * rest_max_iter.  Synchronises the stream. */
+gs_status gs_vcycle_apply(gs_vcycle* vc, const void* f_dev, void* x_dev, gs_solve_stats* stats);
+/* Level l's extents, sites, stored blocks (12 x 12; 0 for level 0, which is
+ * the stencil) and the number of probe colours used to assemble level l + 1
+ * (0 for the coarsest). */
+gs_status gs_vcycle_level(const gs_vcycle* vc, int level, int dims_out[4], int64_t* sites,
+                          int64_t* blocks, int* colours);
+/* y = A_level x for level >= 1, in the level's natural order (level l - 1's
+ * coarse labels): the assembled coarse operator.  complex128 [sites][4][3]. */
+gs_status gs_vcycle_operator_apply(gs_vcycle* vc, int level, const void* x_dev, void* y_dev);
+
+/* BiCGStab (van der Vorst) on the whole system D x = f, to tol in the
+ * recursively updated residual, right-preconditioned by one V-cycle per
+ * application when vc != NULL (Section 4's preconditioned solver; x is
+ * accumulated from the preconditioned directions actually applied, so an
+ * inexact V-cycle still gives the x whose residual the recursion tracks),
+ * plain when vc == NULL.  f_dev, x_dev complex128 [V][4][3], site order.
+ * stats: outer_iters = steps, true_residual = ||f - D x|| / ||f|| recomputed
+ * in FP64, outer_residual = the recursive one, rest-set counts as for
+ * gs_vcycle_apply.  *rate_out (may be NULL) = Section 4's average
+ * convergence rate R = (||r_n|| / ||r_0||)^(1/n) over the n steps taken;
+ * history (may be NULL) receives ||r_0||, ||r_1||, ... (-1 past the end),
+ * history_cap entries at most.  GS_MAXITER after max_iter steps (x = the last
+ * iterate).  Synchronises the stream. */
+gs_status gs_solve_bicgstab(gs_ctx* ctx, gs_vcycle* vc, const void* f_dev, void* x_dev, double tol,
+                            int max_iter, gs_solve_stats* stats, double* rate_out, double* history,
+                            int history_cap);
+
 /* Text of the last error on this context ("" if none).  The pointer stays
  * valid until the next call on the context. */
 const char* gs_last_error(const gs_ctx* ctx);

@@ -7,7 +7,7 @@ The compute path is the CUDA library ``libgschur.so`` (C ABI in
 callers only for device memory and streams.
 """
 from ._binding import *  # noqa: F401,F403
-from ._binding import (Context, GschurError, EXPORTS, LIB_PATH, Net, gs_default_opts,  # noqa: F401
+from ._binding import (Context, GschurError, EXPORTS, LIB_PATH, Net, VCycle, gs_default_opts,  # noqa: F401
                        gs_solve_opts, gs_solve_stats, lib)
 
 __all__ = ["Context", "GschurError", "gs_create", "gs_destroy", "gs_set_gauge",
@@ -23,4 +23,4 @@ __all__ = ["Context", "GschurError", "gs_create", "gs_destroy", "gs_set_gauge",
            "GS_TYPE_I", "GS_TYPE_II", "GS_F64", "GS_F32", "GS_BF16", "GS_GMRES",
            "GS_BICGSTAB", "GS_OK", "GS_MAXITER", "GS_BREAKDOWN", "STATUS_NAMES",
            "schur_apply_reusken", "GS_OPT_MULTI_BATCH", "GS_OPT_WAIT_LIMIT_US",
-           "gs_selftest_wait", "schur_apply_approx"]
+           "gs_selftest_wait", "schur_apply_approx", "VCycle", "gs_solve_bicgstab"]

@@ -36,7 +36,8 @@ EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson
            "gs_lowp_unpack_multi", "wilson_apply_lowp_multi", "gs_solve_rr", "gs_net_create",
            "gs_net_destroy", "gs_net_set_weights", "gs_net_get", "gs_net_apply",
            "gs_net_train_step", "gs_set_net", "gs_profile_phases", "schur_apply_reusken",
-           "gs_selftest_wait", "schur_apply_approx")
+           "gs_selftest_wait", "schur_apply_approx", "gs_vcycle_create", "gs_vcycle_destroy",
+           "gs_vcycle_apply", "gs_vcycle_level", "gs_vcycle_operator_apply", "gs_solve_bicgstab")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -111,6 +112,17 @@ def _load():
         "schur_apply_reusken": (i32, [vp, i32, i32, i32, vp, vp]),
         "gs_selftest_wait": (i32, [vp, i32]),
         "schur_apply_approx": (i32, [vp, i32, i32, i32, i32, vp, vp]),
+        "gs_vcycle_create": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int), i32, ctypes.c_double, i32,
+                                   ctypes.POINTER(vp)]),
+        "gs_vcycle_destroy": (i32, [vp]),
+        "gs_vcycle_apply": (i32, [vp, vp, vp, ctypes.POINTER(gs_solve_stats)]),
+        "gs_vcycle_level": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int), i64p, i64p,
+                                  ctypes.POINTER(ctypes.c_int)]),
+        "gs_vcycle_operator_apply": (i32, [vp, i32, vp, vp]),
+        "gs_solve_bicgstab": (i32, [vp, vp, vp, vp, ctypes.c_double, i32, ctypes.POINTER(gs_solve_stats),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    i32]),
         "schur_solve_multi": (i32, [vp, i32, i32, i32, i32, vp, vp, ctypes.POINTER(gs_solve_opts),
                                     ctypes.POINTER(gs_solve_stats)]),
         "schur_solve_batched": (i32, [i32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
@@ -449,6 +461,72 @@ def wilson_apply_lowp(ctx, ptype, dir, inverse, prec, x_lp, y_lp):
                                              _ptr(x_lp), _ptr(y_lp)))
 
 
+class VCycle:
+    """Owns one gs_vcycle of a context (Section 4's V-cycle preconditioner).
+    levels: one (type, dir, inverse) per coarsening step."""
+
+    def __init__(self, ctx, levels, order=2, rest_tol=1e-2, rest_max_iter=100000):
+        n = len(levels)
+        IA = ctypes.c_int * max(n, 1)
+        ty = IA(*[int(l[0]) for l in levels])
+        di = IA(*[int(l[1]) for l in levels])
+        iv = IA(*[int(bool(l[2])) for l in levels])
+        h = ctypes.c_void_p()
+        self.ctx = ctx
+        self.handle = None
+        _check(ctx.handle, lib.gs_vcycle_create(ctx.handle, n, ty, di, iv, int(order),
+                                                float(rest_tol), int(rest_max_iter),
+                                                ctypes.byref(h)))
+        self.handle = h.value
+        self.nlevels = n + 1
+
+    def apply(self, f, x):
+        self.ctx._need_lattice(f=f, x=x)
+        st = gs_solve_stats()
+        _check(self.ctx.handle, lib.gs_vcycle_apply(self.handle, _ptr(f), _ptr(x), ctypes.byref(st)))
+        return st
+
+    def level(self, l):
+        d = (ctypes.c_int * 4)()
+        n, b, cc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        st = lib.gs_vcycle_level(self.handle, int(l), d, ctypes.byref(n), ctypes.byref(b),
+                                 ctypes.byref(cc))
+        if st != GS_OK:
+            raise GschurError(st, "gs_vcycle_level failed")
+        return {"dims": tuple(d), "sites": n.value, "blocks": b.value, "colours": cc.value}
+
+    def operator_apply(self, l, x, y):
+        sites = self.level(l)["sites"]
+        _need(x, sites * SPINOR_BYTES, "x")
+        _need(y, sites * SPINOR_BYTES, "y")
+        return _check(self.ctx.handle, lib.gs_vcycle_operator_apply(self.handle, int(l), _ptr(x),
+                                                                    _ptr(y)))
+
+    def close(self):
+        if self.handle:
+            lib.gs_vcycle_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gs_solve_bicgstab(ctx, vc, f, x, tol=1e-8, max_iter=3000, history_cap=4096,
+                      allow=(GS_OK,)):
+    """BiCGStab on D x = f (right-preconditioned by the V-cycle vc, or plain if
+    None).  Returns (stats, R, residual history)."""
+    st = gs_solve_stats()
+    R = ctypes.c_double()
+    hist = (ctypes.c_double * history_cap)()
+    _check(ctx, lib.gs_solve_bicgstab(ctx, vc.handle if vc is not None else None, _ptr(f), _ptr(x),
+                                      float(tol), int(max_iter), ctypes.byref(st), ctypes.byref(R),
+                                      hist, int(history_cap)), allow)
+    return st, R.value, [h for h in hist if h >= 0.0]
+
+
 class Context:
     """Owns one gs_ctx; methods forward to the functions above."""
 
@@ -526,6 +604,10 @@ class Context:
 
     def selftest_wait(self, which):
         return gs_selftest_wait(self.handle, which)
+
+    def solve_bicgstab(self, vc, f, x, tol=1e-8, max_iter=3000, allow=(GS_OK,)):
+        self._need_lattice(f=f, x=x)
+        return gs_solve_bicgstab(self.handle, vc, f, x, tol, max_iter, allow=allow)
 
     def schur_apply_reusken(self, ptype, dir, inverse, xb, yb):
         return schur_apply_reusken(self.handle, ptype, dir, inverse, xb, yb)

@@ -239,6 +239,8 @@ gs_status get_plan(gs_ctx* c, int type, int dir, int inverse, Plan** out);
 gs_status pack_plan_links(gs_ctx* c, Plan* p);
 void free_plan(Plan* p);
 gs_status launch_gather(gs_ctx* c, const int32_t* perm, const double2* x, double2* y, int64_t n);
+gs_status build_labels(gs_ctx* c, const int dims[4], int type, int dir, int inverse,
+                       int32_t* perm_dev, int32_t* label_dev, int64_t* nb_out);
 gs_status launch_scatter(gs_ctx* c, const int32_t* perm, const double2* x, double2* y, int64_t n);
 
 // stencil (dslash_f64.cu) -------------------------------------------------------

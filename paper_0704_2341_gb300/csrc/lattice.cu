@@ -280,6 +280,40 @@ gs_status get_plan(gs_ctx* c, int type, int dir, int inverse, Plan** out) {
     return GS_OK;
 }
 
+// The same label order for a lattice of any extents (the coarse "lattices"
+// of the V-cycle's lower levels): perm_dev / label_dev (int32 [V], device)
+// receive p (or q = p^-1 when inverse) and its inverse, *nb_out the coarse
+// count.  The extents blocked by the type must be even.
+gs_status build_labels(gs_ctx* c, const int dims[4], int type, int dir, int inverse,
+                       int32_t* perm_dev, int32_t* label_dev, int64_t* nb_out) {
+    if (type != GS_TYPE_I && type != GS_TYPE_II)
+        return set_err(c, GS_EINVAL, "unknown permutation type %d", type);
+    if (type == GS_TYPE_I) {
+        dir = 0;
+        for (int mu = 0; mu < 4; ++mu)
+            if (dims[mu] % 2)
+                return set_err(c, GS_EINVAL, "Type I blocking needs even extents (L%d = %d)", mu, dims[mu]);
+    } else {
+        if (dir < 0 || dir > 3) return set_err(c, GS_EINVAL, "Type II direction %d not in 0..3", dir);
+        if (dims[dir] % 2)
+            return set_err(c, GS_EINVAL, "Type II blocking along %d needs an even extent (%d)", dir,
+                           dims[dir]);
+    }
+    Dims d;
+    for (int mu = 0; mu < 4; ++mu) d.L[mu] = dims[mu];
+    const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+    const int64_t nb = coarse_count(dims, type);
+    GS_CUDA(c, cudaMemsetAsync(perm_dev, 0, V * sizeof(int32_t), c->stream));
+    GS_CUDA(c, cudaMemsetAsync(label_dev, 0, V * sizeof(int32_t), c->stream));
+    int32_t* pp = inverse ? label_dev : perm_dev;
+    int32_t* ll = inverse ? perm_dev : label_dev;
+    k_build_labels<<<grid_for(V, 256, c->num_sms * 8), 256, 0, c->stream>>>(d, type, dir, V, nb, pp, ll);
+    c->launches++;
+    GS_CHECK_LAUNCH(c);
+    *nb_out = nb;
+    return GS_OK;
+}
+
 gs_status launch_gather(gs_ctx* c, const int32_t* perm, const double2* x, double2* y,
                         int64_t n) {
     if (n <= 0) return GS_OK;

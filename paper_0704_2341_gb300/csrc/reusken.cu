@@ -14,7 +14,7 @@
 // thread per rest site).
 #include <math.h>
 
-#include "gs_internal.cuh"
+#include "block12.cuh"
 
 namespace gs {
 namespace {
@@ -51,10 +51,7 @@ __global__ void k_reusken_dtinv(const int2* __restrict__ nbr, const double2* __r
         const int64_t j = nb + k;
         double2 A[12][12], B[12][12];
         for (int r = 0; r < 12; ++r)
-            for (int q = 0; q < 12; ++q) {
-                A[r][q] = make_double2(r == q ? diag : 0.0, 0.0);
-                B[r][q] = make_double2(r == q ? 1.0 : 0.0, 0.0);
-            }
+            for (int q = 0; q < 12; ++q) A[r][q] = make_double2(r == q ? diag : 0.0, 0.0);
         for (int mu = 0; mu < 4; ++mu) {
             const int2 n2 = nbr[j * 4 + mu];
             for (int hop = 0; hop < 2; ++hop) {
@@ -77,50 +74,7 @@ __global__ void k_reusken_dtinv(const int2* __restrict__ nbr, const double2* __r
                     }
             }
         }
-        // Gauss-Jordan with partial pivoting: A -> 1, B -> A^-1
-        bool ok = true;
-        for (int c = 0; c < 12 && ok; ++c) {
-            int piv = c;
-            double best = A[c][c].x * A[c][c].x + A[c][c].y * A[c][c].y;
-            for (int r = c + 1; r < 12; ++r) {
-                const double m = A[r][c].x * A[r][c].x + A[r][c].y * A[r][c].y;
-                if (m > best) {
-                    best = m;
-                    piv = r;
-                }
-            }
-            if (!(best > 0.0) || !isfinite(best)) {
-                ok = false;
-                break;
-            }
-            if (piv != c)
-                for (int q = 0; q < 12; ++q) {
-                    const double2 ta = A[c][q], tb = B[c][q];
-                    A[c][q] = A[piv][q];
-                    B[c][q] = B[piv][q];
-                    A[piv][q] = ta;
-                    B[piv][q] = tb;
-                }
-            const double2 pv = A[c][c];
-            const double inv = 1.0 / best;
-            const double2 rp = make_double2(pv.x * inv, -pv.y * inv);   // 1 / pivot
-            for (int q = 0; q < 12; ++q) {
-                A[c][q] = zmul(A[c][q], rp);
-                B[c][q] = zmul(B[c][q], rp);
-            }
-            for (int r = 0; r < 12; ++r) {
-                if (r == c) continue;
-                const double2 f = A[r][c];
-                if (f.x == 0.0 && f.y == 0.0) continue;
-                for (int q = 0; q < 12; ++q) {
-                    const double2 ua = zmul(f, A[c][q]), ub = zmul(f, B[c][q]);
-                    A[r][q].x -= ua.x;
-                    A[r][q].y -= ua.y;
-                    B[r][q].x -= ub.x;
-                    B[r][q].y -= ub.y;
-                }
-            }
-        }
+        const bool ok = invert12(A, B);
         if (!ok) atomicExch(status, 1);
         double2* out = dtinv + k * 144;
         for (int r = 0; r < 12; ++r)

@@ -1,0 +1,187 @@
+"""The V-cycle preconditioner of Section 4 on the GPU, through the C ABI,
+against the oracle (oracle.vcycle, oracle.table1).
+
+* every assembled coarse operator (levels >= 1, including the coarsest) equals
+  the oracle's sparse Section 3 approximation of the level above, element by
+  element, for both orders;
+* one V-cycle application with tight rest-set solves equals the oracle's
+  V-cycle with direct rest-set solves;
+* BiCGStab, plain and preconditioned with rest-set solves to 1e-2 (Table 1's
+  set-up), takes the oracle's number of steps (within one) and reaches its
+  average convergence rate R (within 0.02), on a small heatbath field and on
+  the beta = 5.4 and 5.7 stand-in fields of Table 1.
+"""
+import numpy as np
+import pytest
+
+import lattice_inputs as li
+from oracle import dirac, permute, table1, vcycle
+from tests.gpu_util import close, lib, maxrel, rel, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+I, II = permute.TYPE_I, permute.TYPE_II
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = torch_cuda()
+    return torch, lib()
+
+
+def _ctx(gs, torch, dims, m0, U):
+    ctx = gs.Context(dims, m0, torch.cuda.current_stream().cuda_stream)
+    ctx.set_gauge(to_dev(U, torch))
+    return ctx
+
+
+def _oracle_level_apply(vc, l, x):
+    """A_l x in level l's natural order from the oracle's V-cycle."""
+    if l == len(vc.levels):
+        return vc.coarse_op @ x
+    lev = vc.levels[l]
+    perm, nb = lev["perm"], lev["nb"]
+    Abb, Abr, Arb, Arr = lev["blocks"]
+    xl = x.reshape(-1, 12)[perm]
+    xb, xr = xl[:nb].ravel(), xl[nb:].ravel()
+    yl = np.concatenate([Abb @ xb + Abr @ xr, Arb @ xb + Arr @ xr]).reshape(-1, 12)
+    y = np.empty_like(yl)
+    y[perm] = yl
+    return y.ravel()
+
+
+CASES = [((4, 4, 4, 4), [(I, 0, True)]),
+         ((4, 4, 4, 4), [(II, 0, True), (II, 1, True)]),
+         ((4, 4, 4, 4), [(II, 2, False), (I, 0, False)]),
+         ((8, 4, 4, 4), [(I, 0, False), (II, 0, True)]),
+         ((8, 8, 8, 8), [(I, 0, True), (I, 0, True)])]
+
+
+@pytest.mark.parametrize("order", [2, 1])
+@pytest.mark.parametrize("dims,levels", CASES)
+def test_coarse_operators_match_oracle(env, dims, levels, order):
+    torch, gs = env
+    m0 = -0.5
+    U = li.random_gauge(dims, 0.35, 7)
+    D = dirac.wilson_matrix(U, dims, m0)
+    ovc = vcycle.VCycle(D, dims, levels, schur={2: "reusken", 1: "first"}[order], inner=1e-12)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    vc = gs.VCycle(ctx, levels, order=order, rest_tol=1e-12)
+    rng = np.random.default_rng(5)
+    for l in range(1, len(levels) + 1):
+        n = vc.level(l)["sites"]
+        x = rng.standard_normal(n * 12) + 1j * rng.standard_normal(n * 12)
+        xd = to_dev(x, torch)
+        yd = torch.empty_like(xd)
+        vc.operator_apply(l, xd, yd)
+        torch.cuda.synchronize()
+        got, ref = yd.cpu().numpy(), _oracle_level_apply(ovc, l, x)
+        assert close(got, ref, 1e-12), (l, rel(got, ref), maxrel(got, ref))
+    info = [vc.level(l) for l in range(len(levels) + 1)]
+    assert info[0]["sites"] == li.volume(dims)
+    assert info[-1]["sites"] == ovc.coarse_op.shape[0] // 12
+    vc.close()
+    ctx.close()
+
+
+@pytest.mark.parametrize("order", [2, 1])
+@pytest.mark.parametrize("dims,levels", CASES)
+def test_vcycle_apply_matches_oracle(env, dims, levels, order):
+    """x = V(f) with rest-set solves to 1e-13 against the oracle's V-cycle
+    with exact (direct, or BiCGStab to 1e-13 on 8^4) rest-set solves."""
+    torch, gs = env
+    m0 = -0.5
+    U = li.random_gauge(dims, 0.35, 7)
+    D = dirac.wilson_matrix(U, dims, m0)
+    inner = "direct" if li.volume(dims) <= 512 else 1e-13
+    ovc = vcycle.VCycle(D, dims, levels, schur={2: "reusken", 1: "first"}[order], inner=inner)
+    f = li.gaussian_source(dims, 41).ravel()
+    ref = ovc.apply(f)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    vc = gs.VCycle(ctx, levels, order=order, rest_tol=1e-13)
+    fd = to_dev(f, torch)
+    xd = torch.empty_like(fd)
+    st = vc.apply(fd, xd)
+    got = xd.cpu().numpy()
+    assert close(got, ref, 1e-10), (rel(got, ref), maxrel(got, ref))
+    assert st.inner_solves == 2 * len(levels) and st.lowp_fallbacks == 0
+    vc.close()
+    ctx.close()
+
+
+def _compare_table1(gs, torch, U, dims, m0, levels, plain=True):
+    out = table1.run_field(U, dims, m0, levels, inner_tol=1e-2, maxiter=3000, maxiter_pc=200,
+                           plain=plain)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    f = to_dev(li.gaussian_source(dims, 100), torch)
+    x = torch.empty_like(f)
+    res = {}
+    if plain:
+        st, R, hist = ctx.solve_bicgstab(None, f, x, tol=1e-8, max_iter=3000)
+        res["plain"] = (st, R, hist)
+    vc = gs.VCycle(ctx, levels, order=2, rest_tol=1e-2)
+    st, R, hist = ctx.solve_bicgstab(vc, f, x, tol=1e-8, max_iter=200)
+    res["preconditioned"] = (st, R, hist)
+    D = dirac.wilson_matrix(U, dims, m0)
+    xf = x.cpu().numpy().ravel()
+    fh = f.cpu().numpy().ravel()
+    true_res = np.linalg.norm(fh - D @ xf) / np.linalg.norm(fh)
+    vc.close()
+    ctx.close()
+    return out, res, true_res
+
+
+def _check(out, res, true_res):
+    for name, (st, R, hist) in res.items():
+        o = out[name]
+        assert o["converged"] and st.status == 0
+        assert abs(st.outer_iters - o["iters"]) <= 1, (name, st.outer_iters, o["iters"])
+        assert abs(R - o["R"]) <= 0.02, (name, R, o["R"])
+        assert len(hist) == st.outer_iters + 1
+        assert st.true_residual <= 2e-8
+    assert true_res <= 2e-8
+    if "plain" in res:
+        assert res["preconditioned"][0].outer_iters < res["plain"][0].outer_iters
+
+
+def test_table1_solvers_small_heatbath_field(env):
+    """4^4 plaquette-action field (beta = 5.4, 20 sweeps, seed 3), m0 = -0.6,
+    P_I^T at both coarsening steps (4^4 -> 2^4 -> one site)."""
+    torch, gs = env
+    dims = (4, 4, 4, 4)
+    U = li.heatbath_gauge(dims, 5.4, 20, 3)
+    out, res, tr = _compare_table1(gs, torch, U, dims, -0.6, [(I, 0, True)] * 2)
+    _check(out, res, tr)
+
+
+@pytest.mark.parametrize("beta", [5.4, 5.7])
+def test_table1_column_on_the_stand_in_field(env, beta):
+    """Table 1's set-up (Section 4) on the 8^4 stand-in field of the
+    coupling: kappa = 1/6 (m0 = -1), Gaussian source, D x = f to 1e-8,
+    3-level V-cycle with P_I^T at both steps (8^4 -> 4^4 -> 2^4), rest-set
+    solves by BiCGStab to 1e-2."""
+    torch, gs = env
+    dims, U = li.coupling_gauge(beta, 0)
+    out, res, tr = _compare_table1(gs, torch, U, dims, -1.0, table1.LEVELS[beta])
+    _check(out, res, tr)
+    print("\nbeta %.1f: plain %d steps R %.3f | V-cycle %d steps R %.3f (oracle %d / %.3f, %d / %.3f)"
+          % (beta, res["plain"][0].outer_iters, res["plain"][1], res["preconditioned"][0].outer_iters,
+             res["preconditioned"][1], out["plain"]["iters"], out["plain"]["R"],
+             out["preconditioned"]["iters"], out["preconditioned"]["R"]))
+
+
+def test_vcycle_argument_errors(env):
+    torch, gs = env
+    dims = (4, 4, 4, 4)
+    ctx = _ctx(gs, torch, dims, 0.1, li.random_gauge(dims, 0.3, 1))
+    for levels, kw in [([(3, 0, 0)], {}), ([(I, 0, 0)], {"order": 3}), ([(I, 0, 0)], {"rest_tol": 0.0}),
+                       ([(I, 0, 0)] * 3, {}), ([], {})]:
+        with pytest.raises(gs.GschurError):
+            gs.VCycle(ctx, levels, **kw)
+    big = gs.Context((8, 8, 8, 8), 0.1, torch.cuda.current_stream().cuda_stream)
+    big.set_gauge(to_dev(li.random_gauge((8, 8, 8, 8), 0.3, 1), torch))
+    with pytest.raises(gs.GschurError) as e:                  # coarsest 2048 sites > 1024
+        gs.VCycle(big, [(II, 0, 0)])
+    assert e.value.status == gs.GS_ETOOLARGE
+    big.close()
+    ctx.close()
