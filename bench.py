@@ -10,10 +10,13 @@ residual ||f - D x|| / ||f||.  Field: SU(3) plaquette action at beta = 5.4
 one complex Gaussian source (seed 100).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle instead: each timed step is one complete P_I solve of the same
-workload, each warm-up step one S_bb apply.  Further sections of the line:
+oracle instead on the same step: the four permutations' complete solves,
+one single-threaded oracle process per permutation on four host cores
+(warm-up steps: one S_bb apply per process).  Further sections of the line:
 mixed-precision and learned (network + FGMRES) inner solves on the same
-workload, the low-precision stencil on 32^3 x 64, one source of the
+workload, the 16^3 x 32 Type II mixed-precision workload, Table 1 of the
+paper on the GPU (plain and V-cycle-preconditioned BiCGStab on the three
+stand-in fields), the low-precision stencil on 32^3 x 64, one source of the
 32^3 x 64 learned-preconditioner workload, and (``--batched``) several
 sources and lattices solved together.
 """
@@ -43,8 +46,15 @@ WORKLOAD = ("8^4 SU(3) plaquette action beta=5.4 (200 Cabibbo-Marinari sweeps, c
 PERMS = [(1, 0, 0), (2, 0, 0), (1, 0, 1), (2, 0, 1)]
 FIELD = "8^4 heatbath b5.4"
 M0 = -0.4
-# FP64 peak: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM (the part's nominal 1.25 TFLOP/s)
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+# nominal FP64 rate: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM (1.26 TFLOP/s); the
+# roofline divides by the rate gs_fp64_peak measures on the GPU at hand
+FP64_NOMINAL_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+# Table 1 (Section 4): kappa = 1/6, the coarsening steps of each coupling and the
+# paper's printed values (condition number, R plain, R with the V-cycle)
+TABLE1_LEVELS = {5.4: [(1, 0, 1), (1, 0, 1)], 5.7: [(1, 0, 1), (1, 0, 1)],
+                 5.9: [(2, 0, 1), (2, 1, 1)]}
+TABLE1_PAPER = {5.4: (57, 0.76, 0.05), 5.7: (480, 0.83, 0.16), 5.9: (905, 0.89, 0.48)}
+PERM_NAMES = ["P_I", "P_II", "P_I^T", "P_II^T"]
 # DRAM traffic per launch from one ncu capture, per profiled kernel family
 # (0: the FP64 stencil, 3: the persistent FP64 BiCGStab), with the hash of the
 # sources it was taken on
@@ -140,44 +150,97 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def _cpu_sample_main():
-    """Subprocess: the oracle as it stands on one permutation of the workload."""
-    import numpy as np
+_ORACLE = {}
+
+
+def _oracle_init():
+    """(spawn worker) the workload's D, f and permutations, built once."""
     import lattice_inputs as li
-    from oracle import dirac, permute, schur
-    which = int(os.environ.get("GSCHUR_SAMPLE_PERM", "0"))
-    t, mu, inv = PERMS[which]
+    from oracle import dirac
     dims, U = li.workload_gauge(FIELD)
-    D = dirac.wilson_matrix(U, dims, M0)
-    f = li.gaussian_source(dims, 100).ravel()
-    perm, nb = permute.permutation(dims, t, mu, bool(inv))
-    t0 = time.perf_counter()
-    x, info = schur.schur_solve(D, perm, nb, f, tol=1e-10, m=30, inner="bicgstab",
-                                inner_tol=1e-12)
-    dt = time.perf_counter() - t0
-    res = float(np.linalg.norm(f - D @ x) / np.linalg.norm(f))
-    print(json.dumps({"seconds": dt, "true_residual": res, "outer_iters": info["iters"],
-                      "inner_iters": int(sum(info["inner_iters"]))}))
+    _ORACLE["D"] = dirac.wilson_matrix(U, dims, M0)
+    _ORACLE["f"] = li.gaussian_source(dims, 100).ravel()
+    _ORACLE["dims"] = dims
 
 
-def cpu_baseline(which=0):
-    env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
-    env["GSCHUR_SAMPLE_PERM"] = str(which)
-    env.pop("RANK", None)
-    env.pop("WORLD_SIZE", None)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--_cpu-sample"],
-                       capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        raise RuntimeError("cpu sample failed: " + r.stderr[-2000:])
-    out = json.loads(r.stdout.strip().splitlines()[-1])
+def _oracle_solve(which):
+    """(spawn worker) one complete solve of the workload by the oracle as it
+    stands (outer GMRES(30) to 1e-10, inner BiCGStab to 1e-12)."""
+    from oracle import permute, schur
     t, mu, inv = PERMS[which]
-    name = ["P_I", "P_II", "P_I^T", "P_II^T"][which]
-    return {"value": 1.0 / out["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one complete %s solve of the 8^4 workload (1 of the 4 solves of a step), "
-                      "numpy/scipy FP64 oracle, 1 thread, %.1f s, true residual %.1e"
-                      % (name, out["seconds"], out["true_residual"])}
+    D, f = _ORACLE["D"], _ORACLE["f"]
+    perm, nb = permute.permutation(_ORACLE["dims"], t, mu, bool(inv))
+    t0 = time.time()
+    x, info = schur.schur_solve(D, perm, nb, f, tol=1e-10, m=30, inner="bicgstab", inner_tol=1e-12)
+    t1 = time.time()
+    res = float(np.linalg.norm(f - D @ x) / np.linalg.norm(f))
+    return {"perm": PERM_NAMES[which], "start": t0, "end": t1, "seconds": t1 - t0,
+            "true_residual": res, "outer_iters": info["iters"]}
+
+
+def _oracle_warm(which):
+    """(spawn worker) one S_bb apply of the oracle (a warm-up step)."""
+    from oracle import permute, schur
+    t, mu, inv = PERMS[which]
+    D, f = _ORACLE["D"], _ORACLE["f"]
+    perm, nb = permute.permutation(_ORACLE["dims"], t, mu, bool(inv))
+    S = schur.SchurOperator(D, perm, nb, inner="bicgstab", inner_tol=1e-12)
+    S(f[permute.expand_sites(perm[:nb])])
+    return True
+
+
+def oracle_pool(n=len(PERMS)):
+    """n single-threaded oracle worker processes (spawn: safe after CUDA)."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                             "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        pool = mp.get_context("spawn").Pool(n, initializer=_oracle_init)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return pool
+
+
+def oracle_step(pool):
+    """One step of the workload by the oracle: the four solves at once, one
+    process each.  Returns (wall seconds of the step, per-solve records)."""
+    t0 = time.perf_counter()
+    outs = pool.map(_oracle_solve, range(len(PERMS)))
+    return time.perf_counter() - t0, outs
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline():
+    """The oracle timed on the host's cores: one step (the four permutations'
+    solves, one single-threaded process each, in parallel), plus the
+    single-thread rate of the same solves."""
+    pool = oracle_pool()
+    try:
+        wall, outs = oracle_step(pool)
+    finally:
+        pool.close()
+        pool.join()
+    per = [o["seconds"] for o in outs]
+    return {"value": len(PERMS) / wall, "unit": UNIT, "cores": len(PERMS), "kind": "oracle",
+            "host_cores_available": host_cores(),
+            "sample": "one step of the 8^4 workload: the P_I, P_II, P_I^T, P_II^T solves by the "
+                      "numpy/scipy FP64 oracle as it stands, one single-threaded process per "
+                      "permutation, all four at once; %.1f s wall, max true residual %.1e"
+                      % (wall, max(o["true_residual"] for o in outs)),
+            "single_thread": {"value": len(PERMS) / sum(per), "unit": UNIT, "cores": 1,
+                              "seconds_per_solve": {o["perm"]: o["seconds"] for o in outs}}}
 
 
 def replica_totals(dist, device, times_ms, steps, world):
@@ -197,40 +260,41 @@ def replica_totals(dist, device, times_ms, steps, world):
 
 
 def run_reference(args, rank, world):
-    """The CPU oracle timed as the reference arm (rank 0 only)."""
+    """The CPU oracle timed as the reference arm (rank 0 only), on the same
+    step as the GPU arm (the four permutations' complete solves): the K steps'
+    4 K solves are spread over one single-threaded oracle process per host
+    core, and the timed region is all of them; warm-up: one S_bb apply per
+    permutation per warm-up step."""
     if rank != 0:
         return
-    import numpy as np
     import lattice_inputs as li
-    from oracle import dirac, permute, schur
-    dims, U = li.workload_gauge(FIELD)
-    D = dirac.wilson_matrix(U, dims, M0)
-    f = li.gaussian_source(dims, 100).ravel()
-    perm, nb = permute.permutation(dims, 1)
-    # warm-up steps: one S_bb apply each (same code path, bounded)
-    S = schur.SchurOperator(D, perm, nb, inner="bicgstab", inner_tol=1e-12)
-    bi = permute.expand_sites(perm[:nb])
-    for _ in range(args.warmup):
-        S(f[bi])
-    times = []
-    res = []
-    for _ in range(args.steps):
+    li.workload_gauge(FIELD)          # cache the field before the workers load it
+    cores = max(1, min(host_cores(), len(PERMS) * args.steps))
+    pool = oracle_pool(cores)
+    try:
+        pool.map(_oracle_warm, [k % len(PERMS) for k in range(len(PERMS) * args.warmup)], chunksize=1)
         t0 = time.perf_counter()
-        x, _ = schur.schur_solve(D, perm, nb, f, tol=1e-10, m=30, inner="bicgstab",
-                                 inner_tol=1e-12)
-        times.append(time.perf_counter() - t0)
-        res.append(float(np.linalg.norm(f - D @ x) / np.linalg.norm(f)))
-    tot = sum(times)
-    value = args.steps / tot
+        outs = pool.map(_oracle_solve, [k % len(PERMS) for k in range(len(PERMS) * args.steps)],
+                        chunksize=1)
+        tot = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    worst = max(o["true_residual"] for o in outs)
+    value = len(PERMS) * args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "solves_per_step": 1},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each timed step = one complete P_I solve of the 8^4 "
-                                       "workload by the numpy/scipy FP64 oracle (1 of the 4 "
-                                       "solves of a GPU step); warm-up steps = one S_bb apply; "
-                                       "max true residual %.1e" % max(res)},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "solves_per_step": len(PERMS)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "host_cores_available": host_cores(),
+                             "sample": "the %d steps' %d solves (P_I, P_II, P_I^T, P_II^T of the 8^4 "
+                                       "workload, each step) by the numpy/scipy FP64 oracle as it stands, "
+                                       "spread over %d single-threaded processes, %.1f s wall; warm-up = "
+                                       "one S_bb apply per permutation per warm-up step; max true "
+                                       "residual %.1e" % (args.steps, len(outs), cores, tot, worst),
+                             "single_thread": {"value": len(outs) / sum(o["seconds"] for o in outs),
+                                               "unit": UNIT, "cores": 1}},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -239,6 +303,9 @@ def run_reference(args, rank, world):
 def kernel_case(args):
     """One kernel on a large lattice: `reps` launches timed with CUDA events."""
     dims = tuple(int(v) for v in args.dims.split(","))
+    if args.case == "net_tc":
+        print(json.dumps(net_case(dims, args.reps)), flush=True)
+        return
     out = stencil_roofline(args.case, dims, args.prec, args.variant, args.reps)
     print(json.dumps(out), flush=True)
 
@@ -279,13 +346,15 @@ def stencil_roofline(case, dims, prec_name="f32", variant=0, reps=20):
     p = ctx.profile_read(prec)
     ctx.profile(False)
     ms = p.ms / p.launches
+    fp64_peak = ctx.fp64_peak()
     peaks = _peaks()
     out = {"case": case, "prec": prec_name if case != "wilson_f64" else "f64",
            "variant": ctx.get_option(gs.GS_OPT_STENCIL_VARIANT) if case != "wilson_f64" else None,
            "dims": dims, "sites": V, "launches": p.launches,
            "us_per_launch": 1e3 * ms, "sites_per_s": V / (ms / 1e3),
            "tflops": p.flops / p.launches / (ms / 1e3) / 1e12,
-           "frac_fp64_peak": p.flops / p.launches / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+           "fp64_peak_measured_tflops": fp64_peak,
+           "frac_fp64_peak": p.flops / p.launches / (ms / 1e3) / 1e12 / fp64_peak,
            "gbs": p.bytes / p.launches / (ms / 1e3) / 1e9,
            "frac_hbm": (p.bytes / p.launches / (ms / 1e3) / 1e9 / peaks["hbm_gbs"])
            if peaks.get("hbm_gbs") else None,
@@ -522,6 +591,126 @@ def reusken_section(torch, gs, li, reps=20):
     return out
 
 
+def table1_section(torch, gs, li):
+    """Table 1 of the paper on the GPU (Section 4): D x = f to 1e-8 at kappa =
+    1/6 (m0 = -1) on the 8^4 stand-in field of each coupling, Gaussian source
+    (seed 100), BiCGStab plain and right-preconditioned by the 3-level
+    V-cycle on the Section 3 approximation (P_I^T at both steps for beta =
+    5.4 and 5.7, P_II^T along x0 then x1 for 5.9; rest-set solves by BiCGStab
+    to 1e-2; coarsest level inverted exactly).  Times by CUDA events; the
+    V-cycle's set-up (probing the coarse operators, the coarsest inverse) is
+    reported apart."""
+    li.prepare_gauges([("coupling", b, 0) for b in TABLE1_LEVELS])
+    stream = torch.cuda.current_stream()
+    out = {"workload": "8^4 plaquette-action stand-in fields (beta 5.4 / 5.7 / 5.9, 200 Cabibbo-Marinari "
+                       "sweeps, cold start, seeds 21 / 51 / 71), Wilson kappa = 1/6 (m0 = -1), Gaussian "
+                       "source, D x = f to 1e-8", "columns": {}}
+    for beta, levels in TABLE1_LEVELS.items():
+        dims, U = li.coupling_gauge(beta, 0)
+        ctx = gs.Context(dims, -1.0, stream.cuda_stream)
+        ctx.set_gauge(torch.from_numpy(U).to("cuda"))
+        f = torch.from_numpy(li.gaussian_source(dims, 100)).to("cuda")
+        x = torch.empty_like(f)
+        col = {"paper": dict(zip(("condition", "R_plain", "R_preconditioned"), TABLE1_PAPER[beta])),
+               "levels": [list(l) for l in levels]}
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, R, hist = ctx.solve_bicgstab(None, f, x, tol=1e-8, max_iter=3000,
+                                         allow=(gs.GS_OK, gs.GS_MAXITER, gs.GS_BREAKDOWN))
+        b.record(stream)
+        b.synchronize()
+        col["plain"] = {"status": gs.STATUS_NAMES.get(st.status, st.status), "steps": st.outer_iters,
+                        "R": R, "true_residual": st.true_residual, "ms": a.elapsed_time(b)}
+        t0 = time.perf_counter()
+        vc = gs.VCycle(ctx, levels, order=2, rest_tol=1e-2)
+        setup_s = time.perf_counter() - t0
+        a.record(stream)
+        st, R, hist = ctx.solve_bicgstab(vc, f, x, tol=1e-8, max_iter=300,
+                                         allow=(gs.GS_OK, gs.GS_MAXITER, gs.GS_BREAKDOWN))
+        b.record(stream)
+        b.synchronize()
+        col["preconditioned"] = {"status": gs.STATUS_NAMES.get(st.status, st.status),
+                                 "steps": st.outer_iters, "R": R, "true_residual": st.true_residual,
+                                 "ms": a.elapsed_time(b), "setup_s": setup_s,
+                                 "rest_solves": st.inner_solves, "rest_steps": st.inner_iters,
+                                 "rest_solves_at_limit": st.lowp_fallbacks,
+                                 "levels_sites": [vc.level(l)["sites"] for l in range(vc.nlevels)],
+                                 "probe_colours": [vc.level(l)["colours"] for l in range(vc.nlevels - 1)]}
+        vc.close()
+        ctx.close()
+        out["columns"]["%.1f" % beta] = col
+    return out
+
+
+def mixed_large_section(torch, gs, li):
+    """The 16^3 x 32 mixed-precision workload: exp(i 0.25 H) + 5 APE steps
+    (alpha 0.5, seed 2; made on the GPU), Wilson m0 = -0.3, Type II along x0,
+    one Gaussian source (seed 100), outer GMRES(30) to 1e-10: the complete
+    schur_solve with the plain FP64 inner solve against the FP32 and BF16
+    inner solves (FP64 defect correction), each after one untimed solve."""
+    from lattice_inputs import torchgen
+    stream = torch.cuda.current_stream()
+    dims, U = torchgen.workload_gauge_t("16^3x32 eps0.25 ape5", "cuda")
+    ctx = gs.Context(dims, -0.3, stream.cuda_stream)
+    ctx.set_gauge(U)
+    del U
+    f = torch.from_numpy(li.gaussian_source(dims, 100)).to("cuda")
+    x = torch.empty_like(f)
+    out = {"workload": "16^3x32, exp(i 0.25 H) seed 2 + 5 APE steps (alpha 0.5), Wilson m0=-0.3, Type II "
+                       "along x0, one Gaussian source (seed 100), outer GMRES(30) to 1e-10, back-substitution",
+           "inner": {}}
+    for name, prec in (("f64", gs.GS_F64), ("f32", gs.GS_F32), ("bf16", gs.GS_BF16)):
+        o = gs.gs_default_opts(inner_prec=prec)
+        ctx.schur_solve(2, 0, 0, f, x, o)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = ctx.schur_solve(2, 0, 0, f, x, o)
+        b.record(stream)
+        b.synchronize()
+        out["inner"][name] = {"ms": a.elapsed_time(b), "true_residual": st.true_residual,
+                              "outer_iters": st.outer_iters, "inner_iters": st.inner_iters,
+                              "lowp_cycles": st.lowp_cycles}
+    for name in ("f32", "bf16"):
+        out["inner"][name]["speedup_vs_f64"] = out["inner"]["f64"]["ms"] / out["inner"][name]["ms"]
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def net_case(dims, reps=5):
+    """The learned preconditioner's network (24 channels, identity-like
+    weights, tensor-core kernels) applied `reps` times on one lattice: the
+    command the network's ncu profiles are taken with."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_0704_2341_gb300 as gs
+    from paper_0704_2341_gb300 import learned
+    import lattice_inputs as li
+    from lattice_inputs import torchgen
+    V = li.volume(dims)
+    stream = torch.cuda.current_stream()
+    ctx = gs.Context(dims, -0.38, stream.cuda_stream)
+    ctx.set_gauge(torchgen.random_gauge_t(dims, 0.2, 5, "cuda"))
+    net = gs.Net(24)
+    for layer, w in enumerate(learned.identity_like_weights(24, -0.38, 4)):
+        net.set_weights(layer, w)
+    nr = V - ctx.get_permutation(1, 0, 0, torch.empty(V, dtype=torch.int32, device="cuda"))
+    t = torch.randn(nr, 12, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(t)
+    net.apply(ctx.handle, 1, 0, 0, t, y)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        net.apply(ctx.handle, 1, 0, 0, t, y)
+    b.record(stream)
+    b.synchronize()
+    out = {"case": "net_tc", "dims": dims, "rest_sites": nr, "apply_ms": a.elapsed_time(b) / reps}
+    net.close()
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -533,12 +722,16 @@ def main():
                     help="skip the 32^3x64 low-precision stencil roofline")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-preconditioner sections")
+    ap.add_argument("--no-table1", action="store_true",
+                    help="skip Table 1 on the GPU (plain / V-cycle BiCGStab on three 8^4 fields)")
+    ap.add_argument("--no-mixed-large", action="store_true",
+                    help="skip the 16^3x32 Type II mixed-precision solve")
     ap.add_argument("--batched", action="store_true",
                     help="add the batched multi-lattice multi-source section (about 6 minutes)")
-    ap.add_argument("--only", default=None, choices=["batched", "learned_large", "reusken"],
+    ap.add_argument("--only", default=None,
+                    choices=["batched", "learned_large", "reusken", "table1", "mixed_large"],
                     help="run one section alone and print it")
-    ap.add_argument("--_cpu-sample", action="store_true", dest="cpu_sample")
-    ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp"],
+    ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp", "net_tc"],
                     help="kernel micro-benchmark instead of the solve (for profiling)")
     ap.add_argument("--prec", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
@@ -546,9 +739,6 @@ def main():
     ap.add_argument("--dims", default="24,24,24,48")
     ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()
-    if args.cpu_sample:
-        _cpu_sample_main()
-        return
     if args.case:
         kernel_case(args)
         return
@@ -559,7 +749,8 @@ def main():
         import paper_0704_2341_gb300 as gs
         import lattice_inputs as li
         out = {"batched": batched_section, "learned_large": learned_large,
-               "reusken": reusken_section}[args.only](torch, gs, li)
+               "reusken": reusken_section, "table1": table1_section,
+               "mixed_large": mixed_large_section}[args.only](torch, gs, li)
         print(json.dumps(out), flush=True)
         return
 
@@ -578,6 +769,16 @@ def main():
     g.build()
     import paper_0704_2341_gb300 as gs
     import lattice_inputs as li
+
+    # every seeded field the run needs, generated (in parallel, spawn workers)
+    # before the first GPU call if the cache lacks it
+    specs = [("workload", FIELD, None)]
+    if not args.no_learned:
+        specs += [("training", kind, i) for kind in ("heatbath", "ape") for i in range(8)]
+    if not args.no_table1:
+        specs += [("coupling", b, 0) for b in TABLE1_LEVELS]
+    if local == 0:
+        li.prepare_gauges(specs)
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -645,6 +846,8 @@ def main():
     # the same K steps again with the stencil launches bracketed by events
     ms_prof, _, _, prof = timed(args.steps, profile=True)
 
+    fp64_peak = ctx.fp64_peak()
+
     # end to end: pinned host source in, four solutions out, every step
     f_host = torch.from_numpy(f_np).pin_memory()
     x_host = [torch.empty_like(f_host).pin_memory() for _ in PERMS]
@@ -709,10 +912,12 @@ def main():
     traffic = _ncu_traffic_per_launch(dom)
     roofline = {
         "kernel": fam_names[dom],
-        "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-        "peak_source": "FP64 ALU: 152 SMs x 2.07 GHz x 4 flop/clk/SM (nominal 1.25 TFLOP/s; "
-                       "no FP64 entry in MEASURED_PEAKS.json)",
+        "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": achieved / fp64_peak, "traffic": traffic,
+        "peak_source": "FP64 ALU, measured in this run by gs_fp64_peak (8 independent FMA chains per "
+                       "thread, 8 x 256 threads per SM, CUDA events; MEASURED_PEAKS.json has no FP64 "
+                       "entry); nominal 152 SMs x 2.07 GHz x 4 flop/clk = %.3f TFLOP/s"
+                       % FP64_NOMINAL_TFLOPS,
         "launches": prof[dom].launches, "avg_launch_us": 1e3 * avg_ms,
         "algorithmic_flops_per_launch": flops_per_launch,
         "algorithmic_bytes_per_launch": bytes_per_launch,
@@ -731,7 +936,7 @@ def main():
         o_ms, o_fl, o_by, o_ach = fam_view(prof[fam])
         roofline["other_kernels"][fam_names[fam]] = {
             "launches": prof[fam].launches, "avg_launch_us": 1e3 * o_ms,
-            "achieved_tflops": o_ach, "frac_fp64_alu": o_ach / FP64_PEAK_TFLOPS,
+            "achieved_tflops": o_ach, "frac_fp64_alu": o_ach / fp64_peak,
             "share_of_step": prof[fam].ms / ms_prof if ms_prof > 0 else None}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -753,6 +958,10 @@ def main():
     line["mixed_inner"] = mixed
     if not args.no_learned:
         line["learned_mixed"] = learned_headline(args, torch, gs, li, ctx, f, x, stream, value)
+    if not args.no_mixed_large:
+        line["mixed_16x16x16x32"] = mixed_large_section(torch, gs, li)
+    if not args.no_table1:
+        line["table1_gpu"] = table1_section(torch, gs, li)
     if not args.no_lowp_dslash:
         ctx.close()
         ctx = None
@@ -773,7 +982,7 @@ def main():
         torch.cuda.empty_cache()
         line["learned_32x32x32x64"] = learned_large(torch, gs, li)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(0)
+        line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
     if ctx is not None:
         ctx.close()

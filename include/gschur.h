@@ -284,6 +284,13 @@ gs_status gs_profile_read(gs_ctx* ctx, int family, gs_kernel_profile* out);
  * n >= 15.  A diagnostic of where an iteration's time goes; synchronises. */
 gs_status gs_profile_phases(gs_ctx* ctx, double* out, int n);
 
+/* The FP64 peak of this GPU as measured here (the denominator of the FP64
+ * rooflines): a kernel of 8 independent FMA chains per thread on 8 blocks of
+ * 256 threads per SM, timed with CUDA events on the context's stream, the
+ * fastest of 5 launches after one warm-up; *tflops_out = 2 x FMAs / time, in
+ * TFLOP/s.  Synchronises the stream. */
+gs_status gs_fp64_peak(gs_ctx* ctx, double* tflops_out);
+
 /* Low-precision vectors and stencil: the arithmetic of the mixed inner solve
  * (GS_F32 / GS_BF16 storage, FP32 arithmetic, links stored as two rows of
  * -1/2 U with the third row rebuilt as the SU(3) cross product).

@@ -401,6 +401,46 @@ def prepare_training_gauges(kind, n=8, processes=8):
         pool.map(_make_training_gauge, todo)
 
 
+def _make_gauge(spec):
+    kind, a, b = spec
+    if kind == "training":
+        training_gauge(a, b)
+    elif kind == "coupling":
+        coupling_gauge(a, b)
+    else:
+        workload_gauge(a)
+    return True
+
+
+def _gauge_cached(spec):
+    import os
+    kind, a, b = spec
+    if kind == "training":
+        key = ("train_8p4_heatbath_b5.4_s%d" % (11 + b)) if a == "heatbath" else \
+            ("train_8p4_eps0.2_ape10_s%d" % (100 + b))
+    elif kind == "coupling":
+        key = "coupling_8p4_b%.2f_s%d" % (a, 21 + int(b) + int(round(100 * (a - 5.4))))
+    else:
+        key = a.replace("^", "p").replace(" ", "_")
+    return os.path.exists(_cache_path(key))
+
+
+def prepare_gauges(specs, processes=16):
+    """Fill the field cache for several fields at once, generating the missing
+    ones in parallel worker processes (started with ``spawn``, so this is safe
+    in a process that already uses CUDA).  specs: ("training", kind, i),
+    ("coupling", beta, index) or ("workload", name, None)."""
+    import multiprocessing as mp
+    import os
+    todo = [tuple(sp) for sp in specs if not _gauge_cached(sp)]
+    if not todo:
+        return 0
+    n = max(1, min(processes, len(todo), os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(n) as pool:
+        pool.map(_make_gauge, todo)
+    return len(todo)
+
+
 def workload_gauge(name):
     """The seeded gauge field of one of the named workloads.
 

@@ -37,7 +37,8 @@ EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson
            "gs_net_destroy", "gs_net_set_weights", "gs_net_get", "gs_net_apply",
            "gs_net_train_step", "gs_set_net", "gs_profile_phases", "schur_apply_reusken",
            "gs_selftest_wait", "schur_apply_approx", "gs_vcycle_create", "gs_vcycle_destroy",
-           "gs_vcycle_apply", "gs_vcycle_level", "gs_vcycle_operator_apply", "gs_solve_bicgstab")
+           "gs_vcycle_apply", "gs_vcycle_level", "gs_vcycle_operator_apply", "gs_solve_bicgstab",
+           "gs_fp64_peak")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -116,6 +117,7 @@ def _load():
                                    ctypes.POINTER(ctypes.c_int), i32, ctypes.c_double, i32,
                                    ctypes.POINTER(vp)]),
         "gs_vcycle_destroy": (i32, [vp]),
+        "gs_fp64_peak": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
         "gs_vcycle_apply": (i32, [vp, vp, vp, ctypes.POINTER(gs_solve_stats)]),
         "gs_vcycle_level": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int), i64p, i64p,
                                   ctypes.POINTER(ctypes.c_int)]),
@@ -604,6 +606,12 @@ class Context:
 
     def selftest_wait(self, which):
         return gs_selftest_wait(self.handle, which)
+
+    def fp64_peak(self):
+        """Measured FP64 TFLOP/s of this GPU (gs_fp64_peak)."""
+        v = ctypes.c_double()
+        _check(self.handle, lib.gs_fp64_peak(self.handle, ctypes.byref(v)))
+        return v.value
 
     def solve_bicgstab(self, vc, f, x, tol=1e-8, max_iter=3000, allow=(GS_OK,)):
         self._need_lattice(f=f, x=x)

@@ -95,6 +95,28 @@ gs_status prof_end_work(gs_ctx* c, int slot, int prec, long long sites, long lon
 
 using namespace gs;
 
+namespace {
+
+// FP64 issue-rate probe: every thread runs kChains independent FMA chains
+// (no chain waits on another), so the FP64 pipe, not latency, sets the rate.
+constexpr int kChains = 8;
+__global__ void __launch_bounds__(256) k_fp64_peak(double* out, int iters, double seed) {
+    double a[kChains];
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) a[q] = seed + 1e-3 * (q + threadIdx.x);
+    const double m = 0.999999999, d = 1e-12;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < kChains; ++q) a[q] = fma(a[q], m, d);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) s += a[q];
+    if (s == 1234.5678) out[blockIdx.x] = s;   // never true; keeps the chains live
+}
+
+}  // namespace
+
 extern "C" {
 
 gs_status gs_profile(gs_ctx* c, int enable) {
@@ -142,6 +164,31 @@ gs_status gs_profile_read(gs_ctx* c, int prec, gs_kernel_profile* out) {
     gs_status s = prof_harvest(c);
     if (s != GS_OK) return s;
     *out = c->prof.tot[prec];
+    return GS_OK;
+}
+
+gs_status gs_fp64_peak(gs_ctx* c, double* tflops_out) {
+    if (!c || !tflops_out) return GS_EINVAL;
+    const int blocks = c->num_sms * 8, iters = 1 << 14;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GS_CUDA(c, cudaEventCreate(&e0));
+    GS_CUDA(c, cudaEventCreate(&e1));
+    double* sink = c->scal_dev;
+    float best = 0.f;
+    for (int rep = 0; rep < 6; ++rep) {   // the first launch warms up; the fastest counts
+        GS_CUDA(c, cudaEventRecord(e0, c->stream));
+        k_fp64_peak<<<blocks, 256, 0, c->stream>>>(sink, iters, 1.0);
+        GS_CUDA(c, cudaEventRecord(e1, c->stream));
+        GS_CUDA(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        GS_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+    }
+    c->launches += 6;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double flops = 2.0 * kChains * (double)iters * blocks * 256.0;
+    *tflops_out = best > 0.f ? flops / (best * 1e-3) / 1e12 : 0.0;
     return GS_OK;
 }
 
