@@ -142,7 +142,7 @@ gs_status gs_set_gauge(gs_ctx* ctx, const void* U_dev);
  * returns the forced value, or under autotuning the variant chosen most
  * recently. */
 enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 3, GS_OPT_MULTI_BATCH = 4,
-       GS_OPT_WAIT_LIMIT_US = 5 };
+       GS_OPT_WAIT_LIMIT_US = 5, GS_OPT_COOP_BLOCKS = 6 };
 /* GS_OPT_INNER_KERNEL: 0 = each inner BiCGStab solve runs as one persistent
  * cooperative kernel (grid barriers with bounded waits between its phases;
  * the default), 1 = five kernel launches per iteration with the convergence
@@ -162,7 +162,11 @@ enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 
  * persistent solvers and the mbarrier waits of the tensor-core network
  * kernels [1000000, i.e. 1 s].  A wait that runs out makes its kernel stop,
  * release what it holds (tensor memory) and report GS_TIMEOUT; the context
- * stays usable. */
+ * stays usable.
+ * GS_OPT_COOP_BLOCKS: the number of blocks this context's persistent
+ * (cooperative) solver kernels use while schur_solve_batched runs several
+ * problems at once; 0 = the problem's share of the SMs, in proportion to its
+ * V x nrhs (the default). */
 gs_status gs_set_option(gs_ctx* ctx, int option, int value);
 gs_status gs_get_option(gs_ctx* ctx, int option, int* value);
 
@@ -275,13 +279,20 @@ gs_status gs_profile(gs_ctx* ctx, int enable);
 enum { GS_PROF_STENCIL_F64 = 0, GS_PROF_STENCIL_F32 = 1, GS_PROF_STENCIL_BF16 = 2,
        GS_PROF_SOLVER_F64 = 3, GS_PROF_SOLVER_LP = 4 };
 gs_status gs_profile_read(gs_ctx* ctx, int family, gs_kernel_profile* out);
+/* The timed launches of a family as intervals: out[2 i], out[2 i + 1] = start
+ * and end of launch i, in ms since a per-device origin common to every
+ * context of the process (so the intervals of concurrent contexts can be
+ * merged); up to cap doubles are written, *n_out receives the number of
+ * launches recorded since profiling was enabled.  Synchronises the stream. */
+gs_status gs_profile_timeline(gs_ctx* ctx, int family, double* out, int cap, int* n_out);
 /* SM clock cycles that block 0 of the persistent FP64 BiCGStab spent in each
  * phase of its iterations while profiling was on (summed over launches):
- * out[3 s + 0] = work of step s (s = 0: v = D p and <rhat, v>; 1: s = r - a v;
- * 2: t = D s, <t, s>, <t, t>; 3: x, r updates, <rhat, r>, ||r||^2; 4: the
- * p update), out[3 s + 1] = its grid barrier, out[3 s + 2] = the reduction of
- * the per-block partials and the scalar algebra after it (0 for step 4).
- * n >= 15.  A diagnostic of where an iteration's time goes; synchronises. */
+ * out[3 s + 0] = work of step s (s = 0: v = D p and <rhat, v>; 1: s = r - a v
+ * and ||s||^2; 2: t = D s, <t, s>, <t, t>, <rhat, t>; 3: the x, r and p
+ * updates and ||r||^2; 4: unused, 0), out[3 s + 1] = its grid barrier,
+ * out[3 s + 2] = the reduction of the per-block partials and the scalar
+ * algebra after it.  n >= 15.  A diagnostic of where an iteration's time
+ * goes; synchronises. */
 gs_status gs_profile_phases(gs_ctx* ctx, double* out, int n);
 
 /* The FP64 peak of this GPU as measured here (the denominator of the FP64
@@ -329,11 +340,15 @@ gs_status schur_solve_multi(gs_ctx* ctx, int type, int dir, int inverse, int nrh
                             gs_solve_stats* stats);
 
 /* Several problems -- lattices with their own contexts, permutations and
- * source counts -- solved concurrently: problem i is schur_solve_multi on
- * ctxs[i] (its own stream) with type[i], dir[i], inverse[i], nrhs[i],
- * f_dev[i], x_dev[i]; each problem's persistent kernels get a share of the
- * SMs proportional to V x nrhs.  The contexts must be distinct.  stats (may
- * be NULL) is an array of nprob entries.  Returns the worst status. */
+ * source counts -- solved concurrently, one host thread per problem: problem
+ * i is schur_solve_multi on ctxs[i] (its own stream) with type[i], dir[i],
+ * inverse[i], nrhs[i], f_dev[i], x_dev[i] -- or schur_solve when nrhs[i] is 1
+ * (with plain FP64 inner solves, opts->inner_prec = GS_F64, every nrhs[i]
+ * must be 1); each
+ * problem's persistent kernels get a share of the SMs proportional to
+ * V x nrhs (GS_OPT_COOP_BLOCKS overrides it per context).  The contexts must
+ * be distinct (they may hold the same lattice and field).  stats (may be
+ * NULL) is an array of nprob entries.  Returns the worst status. */
 gs_status schur_solve_batched(int nprob, gs_ctx* const* ctxs, const int* type, const int* dir,
                               const int* inverse, const int* nrhs, const void* const* f_dev,
                               void* const* x_dev, const gs_solve_opts* opts,

@@ -23,7 +23,7 @@ GS_F64, GS_F32, GS_BF16 = 0, 1, 2
 GS_GMRES, GS_BICGSTAB = 0, 1
 GS_INNER_BICGSTAB, GS_INNER_FGMRES_NET = 0, 1
 GS_OPT_STENCIL_VARIANT, GS_OPT_INNER_KERNEL, GS_OPT_NET_KERNEL, GS_OPT_MULTI_BATCH, \
-    GS_OPT_WAIT_LIMIT_US = 1, 2, 3, 4, 5
+    GS_OPT_WAIT_LIMIT_US, GS_OPT_COOP_BLOCKS = 1, 2, 3, 4, 5, 6
 GS_PROF_STENCIL_F64, GS_PROF_STENCIL_F32, GS_PROF_STENCIL_BF16, GS_PROF_SOLVER_F64, \
     GS_PROF_SOLVER_LP = range(5)
 
@@ -38,7 +38,7 @@ EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson
            "gs_net_train_step", "gs_set_net", "gs_profile_phases", "schur_apply_reusken",
            "gs_selftest_wait", "schur_apply_approx", "gs_vcycle_create", "gs_vcycle_destroy",
            "gs_vcycle_apply", "gs_vcycle_level", "gs_vcycle_operator_apply", "gs_solve_bicgstab",
-           "gs_fp64_peak")
+           "gs_fp64_peak", "gs_profile_timeline")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -118,6 +118,8 @@ def _load():
                                    ctypes.POINTER(vp)]),
         "gs_vcycle_destroy": (i32, [vp]),
         "gs_fp64_peak": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "gs_profile_timeline": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double), i32,
+                                      ctypes.POINTER(ctypes.c_int)]),
         "gs_vcycle_apply": (i32, [vp, vp, vp, ctypes.POINTER(gs_solve_stats)]),
         "gs_vcycle_level": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int), i64p, i64p,
                                   ctypes.POINTER(ctypes.c_int)]),
@@ -603,6 +605,16 @@ class Context:
 
     def profile_phases(self):
         return gs_profile_phases(self.handle)
+
+    def profile_timeline(self, family):
+        """[(start_ms, end_ms)] of the family's timed launches, on the device's
+        common time origin."""
+        n = ctypes.c_int()
+        _check(self.handle, lib.gs_profile_timeline(self.handle, int(family), None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_double * max(2 * n.value, 1))()
+        _check(self.handle, lib.gs_profile_timeline(self.handle, int(family), buf, 2 * n.value,
+                                                    ctypes.byref(n)))
+        return [(buf[2 * i], buf[2 * i + 1]) for i in range(n.value)]
 
     def selftest_wait(self, which):
         return gs_selftest_wait(self.handle, which)

@@ -204,6 +204,11 @@ gs_status gs_set_option(gs_ctx* c, int option, int value) {
         c->opt_multi_batch = value;
         return GS_OK;
     }
+    if (option == GS_OPT_COOP_BLOCKS) {
+        if (value < 0 || value > 65536) return set_err(c, GS_EINVAL, "cooperative block count %d not in 0..65536", value);
+        c->opt_coop_blocks = value;
+        return GS_OK;
+    }
     if (option == GS_OPT_WAIT_LIMIT_US) {
         if (value < 1 || value > 60000000)
             return set_err(c, GS_EINVAL, "wait limit %d us not in 1..60000000", value);
@@ -233,6 +238,10 @@ gs_status gs_get_option(gs_ctx* c, int option, int* value) {
     }
     if (option == GS_OPT_WAIT_LIMIT_US) {
         *value = (int)(c->wait_ns / 1000ull);
+        return GS_OK;
+    }
+    if (option == GS_OPT_COOP_BLOCKS) {
+        *value = c->opt_coop_blocks;
         return GS_OK;
     }
     return set_err(c, GS_EINVAL, "unknown option %d", option);

@@ -34,11 +34,12 @@ __global__ void __launch_bounds__(kThreads) k_dslash_f64(StencilArgs a) {
     __shared__ double bred[4][kMaxRedVals];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    double e0 = 0.0, e1 = 0.0, e2 = 0.0;  // epilogue partial sums
+    double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // epilogue partial sums
 
     for (int64_t base = (int64_t)blockIdx.x * kSitesPerBlock; base < a.n_out;
          base += (int64_t)gridDim.x * kSitesPerBlock)
-        f64_tile<EPI>(a, base, red, e0, e1, e2);
+        f64_tile<EPI>(a, base, kSitesPerBlock, red, e);
+    double e0 = e[0], e1 = e[1], e2 = e[2];
 
     if constexpr (EPI == EPI_NONE) {
         return;

@@ -139,19 +139,21 @@ __device__ __forceinline__ void hop_mu(const StencilArgs& a, int64_t j, bool val
 }
 
 
-// One tile of 32 output sites: phase 1 (warp w = direction w, both hops, to
-// shared memory) and phase 2 (warp w sums spin component w, adds the diagonal
-// term, negation and addend, stores, and accumulates the epilogue dots).
+// One tile of ts <= 32 output sites (lane l < ts handles site base + l):
+// phase 1 (warp w = direction w, both hops, to shared memory) and phase 2
+// (warp w sums spin component w, adds the diagonal term, negation and addend,
+// stores, and accumulates the epilogue dots into e).
+//   EPI_DOT_RHAT_V: e0 + i e1 = <rhat, out>;  EPI_DOT_TS: e0 + i e1 = <out, s>,
+//   e2 = <out, out>;  EPI_DOT_TSR: as EPI_DOT_TS and e3 + i e4 = <rhat, out>.
 template <int EPI, bool CG = false>
-__device__ __forceinline__ void f64_tile(const StencilArgs& a, int64_t base,
-                                         double (&red)[4][24][kSitesPerBlock], double& e0,
-                                         double& e1, double& e2) {
+__device__ __forceinline__ void f64_tile(const StencilArgs& a, int64_t base, int ts,
+                                         double (&red)[4][24][kSitesPerBlock], double (&e)[5]) {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-        // phase 1: warp `warp` computes direction mu = warp for 32 sites
+        // phase 1: warp `warp` computes direction mu = warp for the tile's sites
     {
         const int64_t k = base + lane;
-        const bool valid = k < a.n_out;
+        const bool valid = lane < ts && k < a.n_out;
         const int64_t j = a.o0 + k;
         double2 up[2][3], lo[2][3];
         switch (warp) {
@@ -171,11 +173,11 @@ __device__ __forceinline__ void f64_tile(const StencilArgs& a, int64_t base,
             }
     }
     __syncthreads();
-    // phase 2: warp w finishes spin component w of the 32 sites
+    // phase 2: warp w finishes spin component w of the tile's sites
     {
         const int spin = warp;
         const int64_t k = base + lane;
-        if (k < a.n_out) {
+        if (lane < ts && k < a.n_out) {
             const int64_t j = a.o0 + k;
             const double2* self = nullptr;
             if (j >= a.a0 && j < a.a1) self = a.inA + (j - a.a0) * kSiteC;
@@ -204,13 +206,18 @@ __device__ __forceinline__ void f64_tile(const StencilArgs& a, int64_t base,
                 dst[c] = make_double2(re, im);
                 if (EPI == EPI_DOT_RHAT_V) {  // <rhat, v> = sum conj(rhat) v
                     const double2 rv = CG ? __ldcg(a.epi_vec + k * kSiteC + spin * 3 + c) : a.epi_vec[k * kSiteC + spin * 3 + c];
-                    e0 = fma(rv.x, re, fma(rv.y, im, e0));
-                    e1 = fma(rv.x, im, fma(-rv.y, re, e1));
-                } else if (EPI == EPI_DOT_TS) {  // <t, s>, <t, t>
+                    e[0] = fma(rv.x, re, fma(rv.y, im, e[0]));
+                    e[1] = fma(rv.x, im, fma(-rv.y, re, e[1]));
+                } else if (EPI == EPI_DOT_TS || EPI == EPI_DOT_TSR) {  // <t, s>, <t, t>
                     const double2 sv = CG ? __ldcg(a.epi_vec + k * kSiteC + spin * 3 + c) : a.epi_vec[k * kSiteC + spin * 3 + c];
-                    e0 = fma(re, sv.x, fma(im, sv.y, e0));
-                    e1 = fma(re, sv.y, fma(-im, sv.x, e1));
-                    e2 = fma(re, re, fma(im, im, e2));
+                    e[0] = fma(re, sv.x, fma(im, sv.y, e[0]));
+                    e[1] = fma(re, sv.y, fma(-im, sv.x, e[1]));
+                    e[2] = fma(re, re, fma(im, im, e[2]));
+                    if (EPI == EPI_DOT_TSR) {  // <rhat, t>
+                        const double2 rv = CG ? __ldcg(a.epi_vec2 + k * kSiteC + spin * 3 + c) : a.epi_vec2[k * kSiteC + spin * 3 + c];
+                        e[3] = fma(rv.x, re, fma(rv.y, im, e[3]));
+                        e[4] = fma(rv.x, im, fma(-rv.y, re, e[4]));
+                    }
                 }
             }
         }

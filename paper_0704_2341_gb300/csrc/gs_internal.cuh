@@ -132,6 +132,7 @@ struct Profiler {
     int* ran_dev = nullptr;           // per slot: 1 if the launch did work (not an early exit)
     int* ran_host = nullptr;          // pinned
     gs_kernel_profile tot[5] = {};    // stencil F64/F32/BF16, persistent solver F64 / low precision
+    std::vector<double> timeline[5];  // per family: (start, end) ms of each launch since the device epoch
     unsigned long long* phases_dev = nullptr;  // [16] cycles per phase of the persistent FP64 solver
 };
 constexpr int kProfSlots = 2048;
@@ -204,6 +205,7 @@ struct gs_ctx {
     int opt_net_kernel = 0;            // 0 = tensor-core network kernels (C = 24), 1 = CUDA cores only
     int opt_multi_batch = 0;           // 0 = by rest-set size, 1 = sources together, 2 = one at a time
     unsigned long long wait_ns = 1000000000ull;  // bound on every device-side wait (GS_OPT_WAIT_LIMIT_US)
+    int opt_coop_blocks = 0;           // blocks of this context's cooperative grids in a batched solve (0 = by share)
     void* persist = nullptr;           // persistent-solver scratch (persistent.cu)
     void* multi = nullptr;             // multi-RHS workspaces (multi.cu)
     int coop_block_cap = 0;            // cap on cooperative grids (0 = whole GPU; batched solves)
@@ -249,7 +251,7 @@ gs_status launch_scatter(gs_ctx* c, const int32_t* perm, const double2* x, doubl
 // where the input vector is split in two label segments: [a0, a1) read from
 // inA + (l - a0)*12 and [a1, b1) read from inB + (l - a1)*12 (b1 == a1: no B).
 // self is the input at the output label when it lies in [a0, b1).
-enum StencilEpi { EPI_NONE = 0, EPI_DOT_RHAT_V = 1, EPI_DOT_TS = 2 };
+enum StencilEpi { EPI_NONE = 0, EPI_DOT_RHAT_V = 1, EPI_DOT_TS = 2, EPI_DOT_TSR = 3 };
 struct StencilArgs {
     double2* out;
     int64_t o0, n_out;
@@ -265,7 +267,8 @@ struct StencilArgs {
     const double2* links;    // plan->links (device)
     // epilogue for the fused inner-solver kernels
     int epi;
-    const double2* epi_vec;  // rhat (EPI_DOT_RHAT_V) or s (EPI_DOT_TS), same indexing as out
+    const double2* epi_vec;  // rhat (EPI_DOT_RHAT_V) or s (EPI_DOT_TS, EPI_DOT_TSR), same indexing as out
+    const double2* epi_vec2; // rhat (EPI_DOT_TSR: also <rhat, t>)
     BicgState* st;
     RedScratch red;
     int* ran;                // profiling: set to 1 if the launch did work, 0 if it exited early

@@ -1325,14 +1325,26 @@ gs_status schur_solve_batched(int nprob, gs_ctx* const* ctxs, const int* type, c
         int cap = (int)(share * c->num_sms * 2.0 + 0.5);
         caps[i] = cap < 4 ? 4 : cap;
     }
+    // a problem of one source (and every problem with plain FP64 inner
+    // solves, which take one source) is the single-source schur_solve, its
+    // persistent solver kernels on its share
+    const bool f64 = opts && opts->inner_prec == GS_F64;
+    if (f64)
+        for (int i = 0; i < nprob; ++i)
+            if (nrhs[i] != 1)
+                return set_err(ctxs[i], GS_EINVAL, "schur_solve_batched with GS_F64 inner solves takes one "
+                                                   "source per problem (nrhs %d)", nrhs[i]);
     std::vector<std::thread> th;
     for (int i = 0; i < nprob; ++i) {
         th.emplace_back([&, i]() {
             gs_ctx* c = ctxs[i];
             const int old = c->coop_block_cap;
-            c->coop_block_cap = nprob > 1 ? caps[i] : 0;
-            res[i] = schur_solve_multi(c, type[i], dir[i], inverse[i], nrhs[i], f_dev[i], x_dev[i], opts,
-                                       &sts[i]);
+            c->coop_block_cap = nprob > 1 ? (c->opt_coop_blocks > 0 ? c->opt_coop_blocks : caps[i]) : old;
+            if (f64 || nrhs[i] == 1)
+                res[i] = schur_solve(c, type[i], dir[i], inverse[i], f_dev[i], x_dev[i], opts, &sts[i]);
+            else
+                res[i] = schur_solve_multi(c, type[i], dir[i], inverse[i], nrhs[i], f_dev[i], x_dev[i],
+                                           opts, &sts[i]);
             c->coop_block_cap = old;
         });
     }

@@ -3,18 +3,20 @@
 // On the lattices of the benchmark (8^4: 3840 rest sites) a BiCGStab
 // iteration is latency bound: five kernel launches, each ending in a
 // reduction tail, cost more than the arithmetic.  Here every block of one
-// co-resident grid runs all iterations; the five phases of an iteration are
+// co-resident grid runs all iterations; the four phases of an iteration are
 // separated by a grid barrier, and each reduction is finished by every block
 // summing the per-block partials in the same fixed order, so all blocks hold
 // bit-identical scalars without another barrier.
 //
 // Grid barrier: one release add per block on an arrival counter that grows
 // through the launch, acquire polls until the barrier's last arrival (see
-// gridsync.cuh).  Every wait is bounded: after kSpinLimit polls or one second
-// of global time the waiting block records GS_TIMEOUT in the error word, the
-// other blocks leave when they see it, and the host reads the status.  The grid is sized with the occupancy calculator and
-// launched with cudaLaunchCooperativeKernel, which refuses grids that cannot
-// be co-resident.
+// gridsync.cuh).  Every wait is bounded: after kSpinLimit polls or the
+// context's wait limit of global time the waiting block records GS_TIMEOUT in
+// the error word, the other blocks leave when they see it, and the host reads
+// the status.  The
+// grid is sized with the occupancy calculator and launched with
+// cudaLaunchCooperativeKernel, which refuses grids that cannot be
+// co-resident.
 //
 // Vectors written inside the kernel are read with L2-only loads (__ldcg):
 // the read-only cache path is not coherent with writes of other blocks of
@@ -27,11 +29,12 @@ namespace gs {
 namespace {
 
 constexpr int kPThreads = 128;
+constexpr int kPart = 8;   // values per block in one slot of the partial sums
 
 // Sum NV values over the block (fixed tree); thread 0 gets the result.
 template <int NV, class T>
 __device__ void block_sum(T (&v)[NV], T (&out)[NV]) {
-    __shared__ T sm[kPThreads / 32][4];
+    __shared__ T sm[kPThreads / 32][kPart];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
@@ -48,36 +51,36 @@ __device__ void block_sum(T (&v)[NV], T (&out)[NV]) {
     __syncthreads();
 }
 
-// Every block adds the partials of all blocks in the same order; the totals
-// land in `tot` of every thread.
+// Every block adds the partials of all blocks in the same order (warp w
+// takes blocks w*32 + lane, w*32 + lane + 128, ...; then a fixed tree), so
+// all blocks hold bit-identical totals; the totals land in every thread.
 template <int NV, class T>
 __device__ void grid_total(const T* partial, T (&tot)[NV]) {
-    __shared__ T sh[4];
-    if (threadIdx.x < 32) {
-        T s[NV];
+    __shared__ T sh[kPThreads / 32][kPart];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T s[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) s[q] = T(0);
-        // L2 loads (written by other blocks before the grid barrier); not
-        // volatile, so the loads of all iterations can be in flight at once
-#pragma unroll 4
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
-            const T* p = partial + (int64_t)b * 4;
+    for (int q = 0; q < NV; ++q) s[q] = T(0);
+    // L2 loads (written by other blocks before the grid barrier); not
+    // volatile, so the loads of all iterations can be in flight at once
+#pragma unroll 2
+    for (int b = warp * 32 + lane; b < (int)gridDim.x; b += kPThreads) {
+        const T* p = partial + (int64_t)b * kPart;
 #pragma unroll
-            for (int q = 0; q < NV; ++q) s[q] += __ldcg(p + q);
-        }
+        for (int q = 0; q < NV; ++q) s[q] += __ldcg(p + q);
+    }
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
+    for (int q = 0; q < NV; ++q) {
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-        }
-        if (threadIdx.x == 0) {
+        for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+    }
+    if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < NV; ++q) sh[q] = s[q];
-        }
+        for (int q = 0; q < NV; ++q) sh[warp][q] = s[q];
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < NV; ++q) tot[q] = sh[q];
+    for (int q = 0; q < NV; ++q) tot[q] = (sh[0][q] + sh[1][q]) + (sh[2][q] + sh[3][q]);
     __syncthreads();
 }
 
@@ -90,7 +93,7 @@ __device__ __forceinline__ void put_partial(T* partial, const T (&v)[NV]) {
     block_sum<NV, T>(vv, b);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int q = 0; q < NV; ++q) partial[(int64_t)blockIdx.x * 4 + q] = b[q];
+        for (int q = 0; q < NV; ++q) partial[(int64_t)blockIdx.x * kPart + q] = b[q];
     }
 }
 
@@ -105,13 +108,14 @@ __device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
 
 struct PArgs64 {
     StencilArgs A;  // v = D_rr p with <rhat, v>
-    StencilArgs C;  // t = D_rr s with <t, s>, <t, t>
+    StencilArgs C;  // t = D_rr s with <t, s>, <t, t>, <rhat, t>
     const double2* b;
     double2 *x, *r, *rhat, *p, *v, *s, *t;
     int64_t n;        // complex entries (12 per site)
+    int ts;           // sites per stencil tile (<= 32)
     double tol;
     int maxit;
-    double* partial;  // [6 slots][gridDim][4]
+    double* partial;  // [6 slots][gridDim][kPart]
     GridSync sync;
     BicgState* st;
     unsigned long long* phases;  // [16] or null: cycles per phase (block 0)
@@ -142,19 +146,31 @@ struct PhaseClock {
     }
 };
 
+// van der Vorst's BiCGStab with four grid barriers per iteration:
+//   A: v = D p, <rhat, v>                      | alpha = rho / <rhat, v>
+//   B: s = r - alpha v, ||s||^2, <rhat, s>     | stop early if ||s|| small
+//   C: t = D s, <t, s>, <t, t>, <rhat, t>      | omega = <t, s> / <t, t>,
+//                                              | rho' = <rhat, s> - omega <rhat, t>
+//   D: x += alpha p + omega s, r = s - omega t,
+//      p = r + beta (p - omega v), ||r||^2     | converged?
+// rho' = <rhat, r'> = <rhat, s - omega t> by linearity, so the x, r and p
+// updates share one phase and the reduction that decides beta comes with t's
+// stencil.  (<rhat, s> vanishes in exact arithmetic, but not in rounding:
+// dropping it stalls the iteration once rhat and r are nearly orthogonal.)
 __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
     __shared__ double red[4][24][kSitesPerBlock];
-    __shared__ double2 sc[4];   // alpha, omega, beta, rho
+    __shared__ double2 sc[5];   // alpha, omega, beta, rho, <rhat, s>
     __shared__ int s_flag;       // 0, or 10 + a failure status
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    const int64_t slot = (int64_t)gridDim.x * 4;
+    const int64_t slot = (int64_t)gridDim.x * kPart;
+    const int ts = P.ts;
     double* part = P.partial;
     bool ok = true;
     int iter = 0;
     double rr = 0.0, bb = 0.0, tol2 = 0.0;
     int status = GS_OK;
-    bool conv = false;
+    bool conv = false, early = false;
 
     // x = 0, r = rhat = p = b, ||b||^2
     {
@@ -185,11 +201,10 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
     while (ok && !conv && status == GS_OK && iter < P.maxit) {
         // A: v = D p, <rhat, v> -> alpha
         {
-            double e0 = 0.0, e1 = 0.0, e2 = 0.0;
-            for (int64_t base = (int64_t)blockIdx.x * kSitesPerBlock; base < P.A.n_out;
-                 base += (int64_t)gridDim.x * kSitesPerBlock)
-                f64_tile<EPI_DOT_RHAT_V, true>(P.A, base, red, e0, e1, e2);
-            double v[2] = {e0, e1};
+            double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int64_t base = (int64_t)blockIdx.x * ts; base < P.A.n_out; base += (int64_t)gridDim.x * ts)
+                f64_tile<EPI_DOT_RHAT_V, true>(P.A, base, ts, red, e);
+            double v[2] = {e[0], e[1]};
             put_partial<2, double>(part + slot, v);
             pc.mark(0);
             if (!(ok = grid_sync(P.sync))) break;
@@ -211,57 +226,67 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 break;
             }
         }
-        // B: s = r - alpha v ; x += alpha p ; ||s||^2
+        // B: s = r - alpha v ; ||s||^2, <rhat, s>
         {
             const double2 al = sc[0];
-            double v[1] = {0.0};
+            double v[3] = {0.0, 0.0, 0.0};
             for (int64_t i = tid; i < P.n; i += nth) {
-                const double2 vi = __ldcg(P.v + i), ri = __ldcg(P.r + i), pi = __ldcg(P.p + i);
+                const double2 vi = __ldcg(P.v + i), ri = __ldcg(P.r + i), hi = __ldcg(P.rhat + i);
                 double2 si;
                 si.x = ri.x - (al.x * vi.x - al.y * vi.y);
                 si.y = ri.y - (al.x * vi.y + al.y * vi.x);
                 P.s[i] = si;
-                double2 xi = __ldcg(P.x + i);
-                xi.x = fma(al.x, pi.x, fma(-al.y, pi.y, xi.x));
-                xi.y = fma(al.x, pi.y, fma(al.y, pi.x, xi.y));
-                P.x[i] = xi;
                 v[0] = fma(si.x, si.x, fma(si.y, si.y, v[0]));
+                v[1] = fma(hi.x, si.x, fma(hi.y, si.y, v[1]));
+                v[2] = fma(hi.x, si.y, fma(-hi.y, si.x, v[2]));
             }
-            put_partial<1, double>(part + 2 * slot, v);
+            put_partial<3, double>(part + 2 * slot, v);
             pc.mark(3);
             if (!(ok = grid_sync(P.sync))) break;
             pc.mark(4);
-            double tot[1];
-            grid_total<1, double>(part + 2 * slot, tot);
+            double tot[3];
+            grid_total<3, double>(part + 2 * slot, tot);
+            if (threadIdx.x == 0) sc[4] = make_double2(tot[1], tot[2]);
             pc.mark(5);
             if (!isfinite(tot[0])) {
                 status = GS_NONFINITE;
                 break;
             }
-            if (tot[0] <= tol2) {
+            if (tot[0] <= tol2) {   // x += alpha p below, after the loop
                 rr = tot[0];
                 ++iter;
-                conv = true;
+                conv = early = true;
                 break;
             }
         }
-        // C: t = D s, <t, s>, <t, t> -> omega
+        // C: t = D s, <t, s>, <t, t>, <rhat, t> -> omega, rho', beta
         {
-            double e0 = 0.0, e1 = 0.0, e2 = 0.0;
-            for (int64_t base = (int64_t)blockIdx.x * kSitesPerBlock; base < P.C.n_out;
-                 base += (int64_t)gridDim.x * kSitesPerBlock)
-                f64_tile<EPI_DOT_TS, true>(P.C, base, red, e0, e1, e2);
-            double v[3] = {e0, e1, e2};
-            put_partial<3, double>(part + 3 * slot, v);
+            double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int64_t base = (int64_t)blockIdx.x * ts; base < P.C.n_out; base += (int64_t)gridDim.x * ts)
+                f64_tile<EPI_DOT_TSR, true>(P.C, base, ts, red, e);
+            put_partial<5, double>(part + 3 * slot, e);
             pc.mark(6);
             if (!(ok = grid_sync(P.sync))) break;
             pc.mark(7);
-            double tot[3];
-            grid_total<3, double>(part + 3 * slot, tot);
+            double tot[5];
+            grid_total<5, double>(part + 3 * slot, tot);
             if (threadIdx.x == 0) {
                 const double inv = tot[2] > 0.0 ? 1.0 / tot[2] : 0.0;
-                sc[1] = make_double2(tot[0] * inv, tot[1] * inv);
-                s_flag = (isfinite(sc[1].x) && isfinite(sc[1].y)) ? 0 : 10 + GS_NONFINITE;
+                const double2 om = make_double2(tot[0] * inv, tot[1] * inv);
+                const double2 rs = sc[4];
+                const double2 rho_new = make_double2(rs.x - (om.x * tot[3] - om.y * tot[4]),
+                                                     rs.y - (om.x * tot[4] + om.y * tot[3]));
+                sc[1] = om;
+                s_flag = (isfinite(om.x) && isfinite(om.y)) ? 0 : 10 + GS_NONFINITE;
+                // beta = (rho' / rho) (alpha / omega); a zero omega or rho' is a
+                // breakdown unless phase D's residual shows convergence
+                if (s_flag == 0 && !(om.x == 0.0 && om.y == 0.0) && !(rho_new.x == 0.0 && rho_new.y == 0.0)) {
+                    sc[2] = zmul(zdiv(rho_new, sc[3]), zdiv(sc[0], om));
+                    sc[3] = rho_new;
+                } else if (s_flag == 0) {
+                    s_flag = 1;     // breakdown pending
+                    sc[2] = make_double2(0.0, 0.0);
+                }
             }
             __syncthreads();
             pc.mark(8);
@@ -270,13 +295,16 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 break;
             }
         }
-        // D: x += omega s ; r = s - omega t ; <rhat, r>, ||r||^2 -> beta
+        // D: x += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v) ; ||r||^2
         {
-            const double2 om = sc[1];
-            double v[3] = {0.0, 0.0, 0.0};
+            const double2 al = sc[0], om = sc[1], be = sc[2];
+            const bool pending = s_flag == 1;
+            double v[1] = {0.0};
             for (int64_t i = tid; i < P.n; i += nth) {
-                const double2 si = __ldcg(P.s + i), ti = __ldcg(P.t + i), hi = __ldcg(P.rhat + i);
-                double2 xi = __ldcg(P.x + i);
+                const double2 si = __ldcg(P.s + i), ti = __ldcg(P.t + i), vi = __ldcg(P.v + i);
+                double2 pi = __ldcg(P.p + i), xi = __ldcg(P.x + i);
+                xi.x = fma(al.x, pi.x, fma(-al.y, pi.y, xi.x));
+                xi.y = fma(al.x, pi.y, fma(al.y, pi.x, xi.y));
                 xi.x = fma(om.x, si.x, fma(-om.y, si.y, xi.x));
                 xi.y = fma(om.x, si.y, fma(om.y, si.x, xi.y));
                 P.x[i] = xi;
@@ -284,19 +312,24 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 ri.x = si.x - (om.x * ti.x - om.y * ti.y);
                 ri.y = si.y - (om.x * ti.y + om.y * ti.x);
                 P.r[i] = ri;
-                v[0] = fma(hi.x, ri.x, fma(hi.y, ri.y, v[0]));
-                v[1] = fma(hi.x, ri.y, fma(-hi.y, ri.x, v[1]));
-                v[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, v[2]));
+                double2 q;
+                q.x = pi.x - (om.x * vi.x - om.y * vi.y);
+                q.y = pi.y - (om.x * vi.y + om.y * vi.x);
+                pi.x = fma(be.x, q.x, fma(-be.y, q.y, ri.x));
+                pi.y = fma(be.x, q.y, fma(be.y, q.x, ri.y));
+                P.p[i] = pi;
+                v[0] = fma(ri.x, ri.x, fma(ri.y, ri.y, v[0]));
             }
-            put_partial<3, double>(part + 4 * slot, v);
+            put_partial<1, double>(part + 4 * slot, v);
             pc.mark(9);
+            ++iter;
             if (!(ok = grid_sync(P.sync))) break;
             pc.mark(10);
-            double tot[3];
-            grid_total<3, double>(part + 4 * slot, tot);
-            ++iter;
-            rr = tot[2];
-            if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
+            double tot[1];
+            grid_total<1, double>(part + 4 * slot, tot);
+            pc.mark(11);
+            rr = tot[0];
+            if (!isfinite(rr)) {
                 status = GS_NONFINITE;
                 break;
             }
@@ -304,34 +337,22 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_f64(PArgs64 P) {
                 conv = true;
                 break;
             }
-            if ((om.x == 0.0 && om.y == 0.0) || (tot[0] == 0.0 && tot[1] == 0.0)) {
+            if (pending) {
                 status = GS_BREAKDOWN;
                 break;
             }
-            if (threadIdx.x == 0) {
-                const double2 rho_new = make_double2(tot[0], tot[1]);
-                sc[2] = zmul(zdiv(rho_new, sc[3]), zdiv(sc[0], om));
-                sc[3] = rho_new;
-            }
-            __syncthreads();
-            pc.mark(11);
         }
-        // E: p = r + beta (p - omega v)
-        {
-            const double2 be = sc[2], om = sc[1];
-            for (int64_t i = tid; i < P.n; i += nth) {
-                const double2 vi = __ldcg(P.v + i), ri = __ldcg(P.r + i);
-                double2 pi = __ldcg(P.p + i);
-                double2 q;
-                q.x = pi.x - (om.x * vi.x - om.y * vi.y);
-                q.y = pi.y - (om.x * vi.y + om.y * vi.x);
-                pi.x = fma(be.x, q.x, fma(-be.y, q.y, ri.x));
-                pi.y = fma(be.x, q.y, fma(be.y, q.x, ri.y));
-                P.p[i] = pi;
-            }
-            pc.mark(12);
-            if (!(ok = grid_sync(P.sync))) break;
-            pc.mark(13);
+    }
+    if (early) {
+        // converged on s: x += alpha p (each thread its own entries; no
+        // other block reads x again)
+        const double2 al = sc[0];
+        for (int64_t i = tid; i < P.n; i += nth) {
+            const double2 pi = __ldcg(P.p + i);
+            double2 xi = __ldcg(P.x + i);
+            xi.x = fma(al.x, pi.x, fma(-al.y, pi.y, xi.x));
+            xi.y = fma(al.x, pi.y, fma(al.y, pi.x, xi.y));
+            P.x[i] = xi;
         }
     }
     pc.flush(P.phases);
@@ -358,7 +379,7 @@ struct PArgsLp {
     int64_t n;            // sites
     float tol;
     int maxit;
-    float* partial;       // [6 slots][gridDim][4]
+    float* partial;       // [6 slots][gridDim][kPart]
     GridSync sync;
     LpState* st;
 };
@@ -412,7 +433,7 @@ __global__ void __launch_bounds__(kPThreads) k_bicg_persistent_lp(PArgsLp P) {
     __shared__ int s_flag;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    const int64_t slot = (int64_t)gridDim.x * 4;
+    const int64_t slot = (int64_t)gridDim.x * kPart;
     float* part = P.partial;
     bool ok = true, conv = false;
     int iter = 0, status = GS_OK;
@@ -656,7 +677,7 @@ struct PersistScratch {
 static gs_status persist_scratch(gs_ctx* c, PersistScratch** out) {
     if (!c->persist) {
         PersistScratch* p = new PersistScratch();
-        if (cudaMalloc(&p->partial, 6 * (size_t)kMaxRedBlocks * 4 * sizeof(double)) != cudaSuccess ||
+        if (cudaMalloc(&p->partial, 6 * (size_t)kMaxRedBlocks * kPart * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&p->words, 4 * sizeof(unsigned int)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(p->partial);
@@ -688,11 +709,17 @@ gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs
     const int64_t want = tiles > (int64_t)c->num_sms ? tiles : (int64_t)c->num_sms;
     const int g = coop_grid(c, k_bicg_persistent_f64, want);
     if (g < 1) return set_err(c, GS_ECUDA, "no co-resident grid for the persistent solver");
+    // tiles of up to 32 sites, no more than the grid needs to cover the rest set
+    // once (3840 sites on 152 blocks: 26 per tile, so every SM shares the work)
+    int64_t ts = (A.n_out + g - 1) / g;
+    if (ts > kSitesPerBlock) ts = kSitesPerBlock;
+    if (ts < 1) ts = 1;
     GS_CUDA(c, cudaMemsetAsync(ps->words, 0, 4 * sizeof(unsigned int), c->stream));
     PArgs64 P;
     memset(&P, 0, sizeof P);
     P.A = A;
     P.C = C;
+    P.C.epi_vec2 = w.rhat;   // <rhat, t> comes with t's stencil
     P.A.st = nullptr;
     P.C.st = nullptr;
     P.A.ran = P.C.ran = nullptr;
@@ -705,6 +732,7 @@ gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs
     P.s = w.s;
     P.t = w.t;
     P.n = n;
+    P.ts = (int)ts;
     P.tol = tol;
     P.maxit = maxit;
     P.partial = (double*)ps->partial;

@@ -1,5 +1,7 @@
 // Live timing of the stencil launches (gs_profile / gs_profile_read) and the
 // algorithmic work each launch represents.
+#include <mutex>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -37,15 +39,41 @@ void stencil_work(const gs_ctx* c, const Plan* p, const StencilArgs& a, long lon
              (a.addend ? 192.0 * a.n_out : 0.0);
 }
 
+// One event per device, recorded when profiling is first enabled there: the
+// common origin of the launch timelines of every context on that device.
+static std::mutex g_epoch_mutex;
+static cudaEvent_t g_epoch[64] = {};
+
+static gs_status device_epoch(gs_ctx* c, cudaEvent_t* out) {
+    int dev = 0;
+    GS_CUDA(c, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_err(c, GS_ECUDA, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_epoch_mutex);
+    if (!g_epoch[dev]) {
+        GS_CUDA(c, cudaEventCreate(&g_epoch[dev]));
+        GS_CUDA(c, cudaEventRecord(g_epoch[dev], c->stream));
+        GS_CUDA(c, cudaEventSynchronize(g_epoch[dev]));
+    }
+    *out = g_epoch[dev];
+    return GS_OK;
+}
+
 gs_status prof_harvest(gs_ctx* c) {
     Profiler& P = c->prof;
     if (P.pending.empty()) return GS_OK;
     GS_CUDA(c, cudaEventSynchronize(P.ev[2 * P.pending.back().slot + 1]));
     GS_CUDA(c, cudaMemcpy(P.ran_host, P.ran_dev, kProfSlots * sizeof(int), cudaMemcpyDeviceToHost));
+    cudaEvent_t epoch = nullptr;
+    gs_status se = device_epoch(c, &epoch);
+    if (se != GS_OK) return se;
     for (const auto& q : P.pending) {
         if (!P.ran_host[q.slot]) continue;  // a queued launch that found the solve finished
-        float ms = 0.f;
+        float ms = 0.f, t0 = 0.f, t1 = 0.f;
         GS_CUDA(c, cudaEventElapsedTime(&ms, P.ev[2 * q.slot], P.ev[2 * q.slot + 1]));
+        GS_CUDA(c, cudaEventElapsedTime(&t0, epoch, P.ev[2 * q.slot]));
+        GS_CUDA(c, cudaEventElapsedTime(&t1, epoch, P.ev[2 * q.slot + 1]));
+        P.timeline[q.prec].push_back(t0);
+        P.timeline[q.prec].push_back(t1);
         gs_kernel_profile& t = P.tot[q.prec];
         t.launches += 1;
         t.ms += ms;
@@ -133,7 +161,10 @@ gs_status gs_profile(gs_ctx* c, int enable) {
         GS_CUDA(c, cudaMemsetAsync(P.phases_dev, 0, 16 * sizeof(unsigned long long), c->stream));
         gs_status s = prof_harvest(c);
         if (s != GS_OK) return s;
+        cudaEvent_t epoch = nullptr;
+        if ((s = device_epoch(c, &epoch)) != GS_OK) return s;
         for (auto& t : P.tot) t = gs_kernel_profile{};
+        for (auto& t : P.timeline) t.clear();
         P.on = true;
     } else {
         gs_status s = prof_harvest(c);
@@ -164,6 +195,18 @@ gs_status gs_profile_read(gs_ctx* c, int prec, gs_kernel_profile* out) {
     gs_status s = prof_harvest(c);
     if (s != GS_OK) return s;
     *out = c->prof.tot[prec];
+    return GS_OK;
+}
+
+gs_status gs_profile_timeline(gs_ctx* c, int family, double* out, int cap, int* n_out) {
+    if (!c || !n_out || (cap > 0 && !out)) return GS_EINVAL;
+    if (family < 0 || family > 4) return set_err(c, GS_EINVAL, "unknown profile family %d", family);
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    gs_status s = prof_harvest(c);
+    if (s != GS_OK) return s;
+    const std::vector<double>& t = c->prof.timeline[family];
+    *n_out = (int)(t.size() / 2);
+    for (int i = 0; i < cap && i < (int)t.size(); ++i) out[i] = t[i];
     return GS_OK;
 }
 

@@ -162,3 +162,38 @@ def test_batch_shape_option_gives_the_same_solutions(env):
     with pytest.raises(gs.GschurError):
         ctx.set_option(gs.GS_OPT_MULTI_BATCH, 3)
     ctx.close()
+
+
+def test_batched_plain_f64_four_permutations_match_one_at_a_time(env):
+    """The benchmark's form: the four permutations of one 8^4 system solved
+    at once by schur_solve_batched with plain FP64 inner solves (one context
+    and stream each, the persistent kernels on SM shares), against the same
+    solves one at a time, and against the oracle's D."""
+    torch, gs = env
+    from oracle import dirac
+    dims, U = li.workload_gauge("8^4 heatbath b5.4")
+    D = dirac.wilson_matrix(U, dims, -0.4)
+    perms = [(1, 0, 0), (2, 0, 0), (1, 0, 1), (2, 0, 1)]
+    streams = [torch.cuda.Stream() for _ in perms]
+    ctxs = [_ctx(gs, torch, dims, -0.4, U, s.cuda_stream) for s in streams]
+    f = to_dev(li.gaussian_source(dims, 100), torch)
+    xs = [torch.empty_like(f) for _ in perms]
+    probs = [dict(ctx=c.handle, type=t, dir=mu, inverse=inv, nrhs=1, f=f, x=x)
+             for c, (t, mu, inv), x in zip(ctxs, perms, xs)]
+    o = gs.gs_default_opts()
+    status, sts = gs.schur_solve_batched(probs, o)
+    torch.cuda.synchronize()
+    assert status == gs.GS_OK
+    fh = f.cpu().numpy().ravel()
+    for (t, mu, inv), c, x, st in zip(perms, ctxs, xs, sts):
+        assert st.true_residual <= 1e-10
+        xb = x.cpu().numpy().ravel()
+        assert np.linalg.norm(fh - D @ xb) <= 1e-10 * np.linalg.norm(fh)
+        x1 = torch.empty_like(f)
+        c.schur_solve(t, mu, inv, f, x1, o)
+        assert close(xb, x1.cpu().numpy(), 1e-8)
+    bad = [dict(p, nrhs=2) for p in probs[:2]]
+    status, _ = gs.schur_solve_batched(bad, o)
+    assert status == gs.GS_EINVAL
+    for c in ctxs:
+        c.close()
