@@ -495,6 +495,34 @@ gs_status gs_solve_bicgstab(gs_ctx* ctx, gs_vcycle* vc, const void* f_dev, void*
                             int max_iter, gs_solve_stats* stats, double* rate_out, double* history,
                             int history_cap);
 
+/* Extreme parts of the spectrum of the context's Wilson operator D (Table 1's
+ * second row, the estimated condition number, read as the 2-norm condition
+ * number sigma_max / sigma_min of D; the eigenvalues nearest the origin
+ * behind the convergence rates of Section 4).
+ *
+ * gs_condition_number: Lanczos (no reorthogonalisation) on the Hermitian
+ * D^H D = gamma_5 D gamma_5 D from start_dev (complex128 [V][4][3], not
+ * zero; the caller draws it); every 20 steps the extreme eigenvalues of the
+ * tridiagonal matrix are found by bisection and their residual estimates
+ * beta_j |last component of the Ritz vector| compared with tol x the
+ * eigenvalue; stops when both meet it (GS_OK) or after max_steps steps
+ * (GS_MAXITER, the last estimates returned).  *kappa_out = sigma_max /
+ * sigma_min, sigma = sqrt(eigenvalue of D^H D); *steps_out (may be NULL)
+ * = steps taken.  Synchronises the stream.
+ *
+ * gs_leftmost_eigenvalues: m steps of Arnoldi (classical Gram-Schmidt twice)
+ * on D from start_dev; the eigenvalues of the m x m Hessenberg matrix (shifted
+ * QR on the host) sorted by real part, then imaginary part; the first
+ * min(k, steps) are written to re_out / im_out, *found_out (may be NULL) =
+ * how many.  An invariant Krylov space ends the iteration early with exact
+ * eigenvalues.  m <= 4096 (the basis takes (m + 1) V x 192 bytes).
+ * Synchronises the stream. */
+gs_status gs_condition_number(gs_ctx* ctx, const void* start_dev, int max_steps, double tol,
+                              double* kappa_out, double* sigma_min_out, double* sigma_max_out,
+                              int* steps_out);
+gs_status gs_leftmost_eigenvalues(gs_ctx* ctx, const void* start_dev, int m, int k, double* re_out,
+                                  double* im_out, int* found_out);
+
 /* Text of the last error on this context ("" if none).  The pointer stays
  * valid until the next call on the context. */
 const char* gs_last_error(const gs_ctx* ctx);

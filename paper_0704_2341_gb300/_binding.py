@@ -38,7 +38,7 @@ EXPORTS = ("gs_create", "gs_destroy", "gs_set_gauge", "gs_default_opts", "wilson
            "gs_net_train_step", "gs_set_net", "gs_profile_phases", "schur_apply_reusken",
            "gs_selftest_wait", "schur_apply_approx", "gs_vcycle_create", "gs_vcycle_destroy",
            "gs_vcycle_apply", "gs_vcycle_level", "gs_vcycle_operator_apply", "gs_solve_bicgstab",
-           "gs_fp64_peak", "gs_profile_timeline")
+           "gs_fp64_peak", "gs_profile_timeline", "gs_condition_number", "gs_leftmost_eigenvalues")
 
 
 class gs_solve_opts(ctypes.Structure):
@@ -118,6 +118,11 @@ def _load():
                                    ctypes.POINTER(vp)]),
         "gs_vcycle_destroy": (i32, [vp]),
         "gs_fp64_peak": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "gs_condition_number": (i32, [vp, vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int)]),
+        "gs_leftmost_eigenvalues": (i32, [vp, vp, i32, i32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
         "gs_profile_timeline": (i32, [vp, i32, ctypes.POINTER(ctypes.c_double), i32,
                                       ctypes.POINTER(ctypes.c_int)]),
         "gs_vcycle_apply": (i32, [vp, vp, vp, ctypes.POINTER(gs_solve_stats)]),
@@ -624,6 +629,23 @@ class Context:
         v = ctypes.c_double()
         _check(self.handle, lib.gs_fp64_peak(self.handle, ctypes.byref(v)))
         return v.value
+
+    def condition_number(self, start, max_steps=20000, tol=1e-6, allow=(GS_OK,)):
+        """(kappa, sigma_min, sigma_max, steps) of D by Lanczos on D^H D."""
+        self._need_lattice(start=start)
+        k, lo, hi, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        _check(self.handle, lib.gs_condition_number(self.handle, _ptr(start), int(max_steps), float(tol),
+                                                    ctypes.byref(k), ctypes.byref(lo), ctypes.byref(hi),
+                                                    ctypes.byref(n)), allow)
+        return k.value, lo.value, hi.value, n.value
+
+    def leftmost_eigenvalues(self, start, m, k=6):
+        """The k eigenvalues of D with the smallest real part from m Arnoldi steps."""
+        self._need_lattice(start=start)
+        re, im, n = (ctypes.c_double * k)(), (ctypes.c_double * k)(), ctypes.c_int()
+        _check(self.handle, lib.gs_leftmost_eigenvalues(self.handle, _ptr(start), int(m), int(k), re, im,
+                                                        ctypes.byref(n)))
+        return [complex(re[i], im[i]) for i in range(n.value)]
 
     def solve_bicgstab(self, vc, f, x, tol=1e-8, max_iter=3000, allow=(GS_OK,)):
         self._need_lattice(f=f, x=x)
