@@ -65,7 +65,7 @@ def test_arnoldi_on_the_whole_space_gives_the_dense_spectrum(env, dims, m0):
 def test_table1_condition_number_and_leftmost_eigenvalue_match_oracle(env):
     """beta = 5.4 stand-in field, kappa = 1/6: the condition number from GPU
     Lanczos (tolerance 1e-6) against the oracle's restarted Lanczos, and the
-    eigenvalues of smallest real part from 600 Arnoldi steps against the
+    eigenvalues of smallest real part from 1200 Arnoldi steps against the
     oracle's restarted Arnoldi."""
     torch, gs = env
     dims, U = li.coupling_gauge(5.4, 0)
@@ -78,12 +78,15 @@ def test_table1_condition_number_and_leftmost_eigenvalue_match_oracle(env):
     start = to_dev(li.gaussian_source(dims, 14), torch)
     t0 = time.time()
     kappa, smin, smax, steps = ctx.condition_number(start, max_steps=20000, tol=1e-6)
-    ev = ctx.leftmost_eigenvalues(start, m=600, k=2)
+    ev = ctx.leftmost_eigenvalues(start, m=1200, k=2)
     gpu_s = time.time() - t0
     assert abs(kappa - kappa_o) <= 1e-4 * kappa_o, (kappa, kappa_o)
     assert abs(smin - smin_o) <= 1e-4 * smin_o and abs(smax - smax_o) <= 1e-4 * smax_o
-    assert abs(ev[0].real - ev_o[0].real) <= 1e-5, (ev, ev_o)
-    assert abs(abs(ev[0].imag) - abs(ev_o[0].imag)) <= 1e-5
+    # gamma_5-hermiticity: D's eigenvalues come in complex-conjugate pairs, so
+    # a converged leftmost pair is symmetric
+    assert abs(ev[0] - np.conj(ev[1])) <= 2e-6, ev
+    assert abs(ev[0].real - ev_o[0].real) <= 2e-6, (ev, ev_o)
+    assert abs(abs(ev[0].imag) - abs(ev_o[0].imag)) <= 2e-6
     print("\ncondition number %.4f (oracle %.4f), %d Lanczos steps; leftmost %s (oracle %s); "
           "GPU %.2f s, oracle %.1f s" % (kappa, kappa_o, steps, ev[0], ev_o[0], gpu_s, oracle_s))
     ctx.close()
