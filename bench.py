@@ -601,7 +601,8 @@ def table1_section(torch, gs, li):
     5.4 and 5.7, P_II^T along x0 then x1 for 5.9; rest-set solves by BiCGStab
     to 1e-2; coarsest level inverted exactly).  Times by CUDA events; the
     V-cycle's set-up (probing the coarse operators, the coarsest inverse) is
-    reported apart."""
+    reported apart.  Also the table's second row on the GPU: the condition
+    number of D and its eigenvalue of smallest real part."""
     li.prepare_gauges([("coupling", b, 0) for b in TABLE1_LEVELS])
     stream = torch.cuda.current_stream()
     out = {"workload": "8^4 plaquette-action stand-in fields (beta 5.4 / 5.7 / 5.9, 200 Cabibbo-Marinari "
@@ -615,6 +616,21 @@ def table1_section(torch, gs, li):
         x = torch.empty_like(f)
         col = {"paper": dict(zip(("condition", "R_plain", "R_preconditioned"), TABLE1_PAPER[beta])),
                "levels": [list(l) for l in levels]}
+        # Table 1's second row: the 2-norm condition number of D (Lanczos on
+        # D^H D to 1e-6), and the eigenvalue of D with the smallest real part
+        # (800 Arnoldi steps); start vector: Gaussian, seed 14
+        start = torch.from_numpy(li.gaussian_source(dims, 14)).to("cuda")
+        t0 = time.perf_counter()
+        kappa, smin, smax, lsteps = ctx.condition_number(start, max_steps=20000, tol=1e-6,
+                                                         allow=(gs.GS_OK, gs.GS_MAXITER))
+        cond_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ev = ctx.leftmost_eigenvalues(start, m=800, k=2)
+        col["condition"] = {"kappa": kappa, "sigma_min": smin, "sigma_max": smax, "lanczos_steps": lsteps,
+                            "seconds": cond_s}
+        col["leftmost_eigenvalue"] = {"re": ev[0].real, "im": abs(ev[0].imag), "arnoldi_steps": 800,
+                                      "seconds": time.perf_counter() - t0}
+        del start
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         st, R, hist = ctx.solve_bicgstab(None, f, x, tol=1e-8, max_iter=3000,
@@ -736,7 +752,7 @@ def main():
     ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp", "net_tc"],
                     help="kernel micro-benchmark instead of the solve (for profiling)")
     ap.add_argument("--prec", default="f32", choices=["f32", "bf16"])
-    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="low-precision stencil variant (0 = autotuned)")
     ap.add_argument("--dims", default="24,24,24,48")
     ap.add_argument("--reps", type=int, default=20)

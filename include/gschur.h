@@ -138,7 +138,9 @@ gs_status gs_set_gauge(gs_ctx* ctx, const void* U_dev);
  * variant is timed with CUDA events when a set is first used), 1 = one
  * thread per site (all eight hops in registers), 3 / 4 = the same with a
  * register budget for 6 / 8 blocks of 128 threads per SM, 2 = one warp per
- * direction (four partial sums combined in shared memory).  gs_get_option
+ * direction (four partial sums combined in shared memory), 5 / 6 = one thread
+ * per site with the next direction's operands loaded while the current one
+ * is computed (register budget for 3 / 4 blocks per SM).  gs_get_option
  * returns the forced value, or under autotuning the variant chosen most
  * recently. */
 enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 3, GS_OPT_MULTI_BATCH = 4,

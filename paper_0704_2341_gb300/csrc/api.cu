@@ -184,7 +184,7 @@ gs_status gs_destroy(gs_ctx* c) {
 gs_status gs_set_option(gs_ctx* c, int option, int value) {
     if (!c) return GS_EINVAL;
     if (option == GS_OPT_STENCIL_VARIANT) {
-        if (value < 0 || value > 4) return set_err(c, GS_EINVAL, "stencil variant %d not in 0..4", value);
+        if (value < 0 || value > 6) return set_err(c, GS_EINVAL, "stencil variant %d not in 0..6", value);
         c->opt_stencil_variant = value;
         invalidate_mixed_links(c);  // re-tune / re-select on next use
         return GS_OK;

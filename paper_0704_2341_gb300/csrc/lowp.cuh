@@ -452,8 +452,187 @@ __device__ __forceinline__ void site_dir(const LpArgs& a, int64_t k, int2 nb, fl
     }
 }
 
+// Raw (still packed) operands of one direction of one site: the two
+// neighbour spinors and the two links, as loaded; unpacked only when used.
+template <class S>
+struct Raw;
+template <>
+struct Raw<float> {
+    float4 pf[6], pb[6], lf[3], lb[3];
+    __device__ __forceinline__ void load(const LpArgs& a, int mu, int64_t jf, int64_t jb, int64_t k) {
+        const float4* in = (const float4*)a.in;
+        const float4* L = (const float4*)a.links + (int64_t)mu * 3 * a.n;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) pf[c] = __ldg(in + c * a.n + jf);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) pb[c] = __ldg(in + c * a.n + jb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) lf[c] = __ldg(L + c * a.n + k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) lb[c] = __ldg(L + c * a.n + jb);
+    }
+    __device__ __forceinline__ static void spinor(const float4 (&v)[6], float (&f)[24]) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            f[4 * c] = v[c].x; f[4 * c + 1] = v[c].y; f[4 * c + 2] = v[c].z; f[4 * c + 3] = v[c].w;
+        }
+    }
+    __device__ __forceinline__ static void link(const float4 (&v)[3], float (&f)[12]) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            f[4 * c] = v[c].x; f[4 * c + 1] = v[c].y; f[4 * c + 2] = v[c].z; f[4 * c + 3] = v[c].w;
+        }
+    }
+    __device__ __forceinline__ void unpack(float (&f)[24], float (&b)[24], float (&u)[12], float (&w)[12]) const {
+        spinor(pf, f);
+        spinor(pb, b);
+        link(lf, u);
+        link(lb, w);
+    }
+};
+template <>
+struct Raw<__nv_bfloat16> {
+    uint4 pf[3], pb[3];
+    uint2 lf[3], lb[3];
+    __device__ __forceinline__ void load(const LpArgs& a, int mu, int64_t jf, int64_t jb, int64_t k) {
+        const uint4* in = (const uint4*)a.in;
+        const uint2* L = (const uint2*)a.links + (int64_t)mu * 3 * a.n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pf[c] = __ldg(in + c * a.n + jf);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pb[c] = __ldg(in + c * a.n + jb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) lf[c] = __ldg(L + c * a.n + k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) lb[c] = __ldg(L + c * a.n + jb);
+    }
+    __device__ __forceinline__ static void spinor(const uint4 (&v)[3], float (&f)[24]) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float2 t;
+            t = unpack_bf2(v[c].x); f[8 * c + 0] = t.x; f[8 * c + 1] = t.y;
+            t = unpack_bf2(v[c].y); f[8 * c + 2] = t.x; f[8 * c + 3] = t.y;
+            t = unpack_bf2(v[c].z); f[8 * c + 4] = t.x; f[8 * c + 5] = t.y;
+            t = unpack_bf2(v[c].w); f[8 * c + 6] = t.x; f[8 * c + 7] = t.y;
+        }
+    }
+    __device__ __forceinline__ static void link(const uint2 (&v)[3], float (&f)[12]) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float2 t;
+            t = unpack_bf2(v[c].x); f[4 * c + 0] = t.x; f[4 * c + 1] = t.y;
+            t = unpack_bf2(v[c].y); f[4 * c + 2] = t.x; f[4 * c + 3] = t.y;
+        }
+    }
+    __device__ __forceinline__ void unpack(float (&f)[24], float (&b)[24], float (&u)[12], float (&w)[12]) const {
+        spinor(pf, f);
+        spinor(pb, b);
+        link(lf, u);
+        link(lb, w);
+    }
+};
+
+// the two hops of direction MU from raw operands (masked hops contribute 0)
+template <class S, int MU>
+__device__ __forceinline__ void raw_dir(const Raw<S>& r, bool hf, bool hb, float (&acc)[24]) {
+    float pf[24], pb[24], lf[12], lb[12];
+    r.unpack(pf, pb, lf, lb);
+    if (hf) {
+        cf h[2][3], u[3][3], g[2][3];
+        project<MU, true>(pf, h);
+        rebuild(lf, u);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                cf t = cmul(u[q][0], h[s][0]);
+                cfma_(t, u[q][1], h[s][1]);
+                cfma_(t, u[q][2], h[s][2]);
+                g[s][q] = t;
+            }
+        accumulate<MU, -1>(acc, g);
+    }
+    if (hb) {
+        cf h[2][3], u[3][3], g[2][3];
+        project<MU, false>(pb, h);
+        rebuild(lb, u);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                cf t = cf{0.f, 0.f};
+                ccfma_(t, u[0][q], h[s][0]);
+                ccfma_(t, u[1][q], h[s][1]);
+                ccfma_(t, u[2][q], h[s][2]);
+                g[s][q] = t;
+            }
+        accumulate<MU, +1>(acc, g);
+    }
+}
+
 template <class S, int EPI>
 __device__ __forceinline__ void lp_finish(const LpArgs& a, LpState* st, float (&tot)[3]);
+
+// Variant "pipelined site": one thread per site, like "site", but the loads of
+// direction mu + 1 are issued before direction mu is computed (two operand
+// buffers in registers, kept packed until used), so each thread waits for
+// memory about twice per site instead of five times; fewer blocks fit per SM.
+template <class S, int EPI, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_dslash_lp_pipe(LpArgs a) {
+    const bool skip = a.st != nullptr && a.st->done;
+    if (a.ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *a.ran = skip ? 0 : 1;
+    if (skip) return;
+    float e[3] = {0.f, 0.f, 0.f};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int4 n01 = __ldg((const int4*)(a.nbr + k * 4));
+        const int4 n23 = __ldg((const int4*)(a.nbr + k * 4) + 1);
+        // out-of-set neighbours (-1) read the site itself and are masked
+        const bool h0f = n01.x >= 0, h0b = n01.y >= 0, h1f = n01.z >= 0, h1b = n01.w >= 0;
+        const bool h2f = n23.x >= 0, h2b = n23.y >= 0, h3f = n23.z >= 0, h3b = n23.w >= 0;
+        Raw<S> r0, r1;
+        r0.load(a, 0, h0f ? n01.x : k, h0b ? n01.y : k, k);
+        r1.load(a, 1, h1f ? n01.z : k, h1b ? n01.w : k, k);
+        float acc[24];
+#pragma unroll
+        for (int q = 0; q < 24; ++q) acc[q] = 0.f;
+        raw_dir<S, 0>(r0, h0f, h0b, acc);
+        r0.load(a, 2, h2f ? n23.x : k, h2b ? n23.y : k, k);
+        raw_dir<S, 1>(r1, h1f, h1b, acc);
+        r1.load(a, 3, h3f ? n23.z : k, h3b ? n23.w : k, k);
+        raw_dir<S, 2>(r0, h2f, h2b, acc);
+        float self[24];
+        Store<S>::load_spinor(a.in, a.n, k, self);
+        raw_dir<S, 3>(r1, h3f, h3b, acc);
+#pragma unroll
+        for (int q = 0; q < 24; ++q) acc[q] = fmaf(a.diag, self[q], acc[q]);
+        Store<S>::store_spinor(a.out, a.n, k, acc);
+        if (EPI == EPI_DOT_RHAT_V) {
+            float rv[24];
+            Store<S>::load_spinor(a.epi_vec, a.n, k, rv);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                e[0] = fmaf(rv[2 * q], acc[2 * q], fmaf(rv[2 * q + 1], acc[2 * q + 1], e[0]));
+                e[1] = fmaf(rv[2 * q], acc[2 * q + 1], fmaf(-rv[2 * q + 1], acc[2 * q], e[1]));
+            }
+        } else if (EPI == EPI_DOT_TS) {
+            float sv[24];
+            Store<S>::load_spinor(a.epi_vec, a.n, k, sv);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                const float tr = acc[2 * q], ti = acc[2 * q + 1];
+                e[0] = fmaf(tr, sv[2 * q], fmaf(ti, sv[2 * q + 1], e[0]));
+                e[1] = fmaf(tr, sv[2 * q + 1], fmaf(-ti, sv[2 * q], e[1]));
+                e[2] = fmaf(tr, tr, fmaf(ti, ti, e[2]));
+            }
+        }
+    }
+    if constexpr (EPI != EPI_NONE) {
+        float tot[3];
+        if (lp_reduce_last<3>(e, a.partial, a.counter, tot) && threadIdx.x == 0)
+            lp_finish<S, EPI>(a, a.st, tot);
+    }
+}
 
 template <class S, int EPI, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_dslash_lp_site(LpArgs a) {

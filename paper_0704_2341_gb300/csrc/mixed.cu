@@ -284,7 +284,8 @@ gs_status launch_lp_stencil(gs_ctx* c, LpArgs a, long long hops, int variant, lo
         }
     } else {
         // variants 1, 3, 4: thread per site with a register budget for
-        // 4, 6 or 8 blocks of 128 threads per SM
+        // 4, 6 or 8 blocks of 128 threads per SM; 5, 6: the same with the
+        // next direction's loads in flight (budget for 3 or 4 blocks)
         const int b = lp_block(a.n, c->num_sms);
         int64_t g = (a.n + b - 1) / b;
         if (a.epi != EPI_NONE && g > kMaxRedBlocks) g = kMaxRedBlocks;
@@ -295,14 +296,26 @@ gs_status launch_lp_stencil(gs_ctx* c, LpArgs a, long long hops, int variant, lo
                 k_dslash_lp_site<S, EPI_DOT_RHAT_V, MB><<<(int)g, b, 0, c->stream>>>(a); break;  \
             default: k_dslash_lp_site<S, EPI_DOT_TS, MB><<<(int)g, b, 0, c->stream>>>(a); break; \
         }
+#define GS_PIPE_LAUNCH(MB)                                                                       \
+        switch (a.epi) {                                                                         \
+            case EPI_NONE: k_dslash_lp_pipe<S, EPI_NONE, MB><<<(int)g, b, 0, c->stream>>>(a); break; \
+            case EPI_DOT_RHAT_V:                                                                 \
+                k_dslash_lp_pipe<S, EPI_DOT_RHAT_V, MB><<<(int)g, b, 0, c->stream>>>(a); break;  \
+            default: k_dslash_lp_pipe<S, EPI_DOT_TS, MB><<<(int)g, b, 0, c->stream>>>(a); break; \
+        }
         if (variant == 3) {
             GS_SITE_LAUNCH(6)
         } else if (variant == 4) {
             GS_SITE_LAUNCH(8)
+        } else if (variant == 5) {
+            GS_PIPE_LAUNCH(3)
+        } else if (variant == 6) {
+            GS_PIPE_LAUNCH(4)
         } else {
             GS_SITE_LAUNCH(4)
         }
 #undef GS_SITE_LAUNCH
+#undef GS_PIPE_LAUNCH
     }
     ++*launches;
     GS_CHECK_LAUNCH(c);
@@ -340,7 +353,8 @@ struct LpPlanData {
     int64_t n = 0;         // sites of the set
     long long hops = 0;    // in-set neighbour terms of one D application
     int variant = 0;       // stencil variant: 1/3/4 = thread per site (register budget for
-                           // 4/6/8 blocks per SM), 2 = warp per direction
+                           // 4/6/8 blocks per SM), 2 = warp per direction, 5/6 = thread per
+                           // site with the next direction's loads in flight (3/4 blocks)
     int2* nbr_r = nullptr;
     void* links = nullptr;
 };
@@ -428,11 +442,11 @@ static gs_status ensure_lp(gs_ctx* c, int prec, int64_t n) {
     return GS_OK;
 }
 
-// The autotuner: time both stencil variants on this set (2 warm-up and 5
-// timed launches each, CUDA events, zeroed operands) and keep the faster one;
+// The autotuner: time every stencil variant on this set (2 warm-up and 5
+// timed launches each, CUDA events, zeroed operands) and keep the fastest;
 // a variant forced with gs_set_option skips the timing.
 static gs_status lp_tune(gs_ctx* c, LpPlanData& pd) {
-    if (c->opt_stencil_variant == 1 || c->opt_stencil_variant == 2) {
+    if (c->opt_stencil_variant != 0) {
         pd.variant = c->opt_stencil_variant;
         return GS_OK;
     }
@@ -456,7 +470,7 @@ static gs_status lp_tune(gs_ctx* c, LpPlanData& pd) {
     float best = 0.f;
     const bool was_on = c->prof.on;
     c->prof.on = false;
-    for (int v = 1; v <= 4; ++v) {
+    for (int v = 1; v <= 6; ++v) {
         long long l = 0;
         for (int r = 0; r < 7; ++r) {
             if (r == 2) GS_CUDA(c, cudaEventRecord(e0, c->stream));

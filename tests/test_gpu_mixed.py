@@ -124,7 +124,7 @@ def test_lowp_tol_validation(env):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("prec,tol", [("f32", 4e-6), ("bf16", 3e-2)])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (3, 4, 2, 5)])
 def test_lowp_stencil_full_lattice(env, prec, tol, dims, variant):
@@ -155,7 +155,7 @@ def test_lowp_stencil_full_lattice(env, prec, tol, dims, variant):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("prec,tol", [("f32", 4e-6), ("bf16", 3e-2)])
 @pytest.mark.parametrize("t,mu,inv", TYPES + [(2, 2, True)])
 def test_lowp_stencil_rest_set(env, prec, tol, t, mu, inv, variant):
@@ -190,7 +190,7 @@ def test_autotuner_picks_a_variant_and_options_validate(env):
     x = to_dev(li.gaussian_source(dims, 1), torch)
     xl = torch.empty(gs.lowp_bytes(V, gs.GS_F32), dtype=torch.uint8, device="cuda:0")
     ctx.lowp_pack(0, 0, 0, gs.GS_F32, x, xl)
-    assert ctx.get_option(gs.GS_OPT_STENCIL_VARIANT) in (1, 2, 3, 4)
+    assert ctx.get_option(gs.GS_OPT_STENCIL_VARIANT) in (1, 2, 3, 4, 5, 6)
     with pytest.raises(gs.GschurError):
         ctx.set_option(gs.GS_OPT_STENCIL_VARIANT, 7)
     with pytest.raises(gs.GschurError):
