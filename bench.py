@@ -19,8 +19,8 @@ mixed-precision and learned (network + FGMRES) inner solves on the same
 workload, the 16^3 x 32 Type II mixed-precision workload, Table 1 of the
 paper on the GPU (plain and V-cycle-preconditioned BiCGStab on the three
 stand-in fields), the low-precision stencil on 32^3 x 64, one source of the
-32^3 x 64 learned-preconditioner workload, and (``--batched``) several
-sources and lattices solved together.
+32^3 x 64 learned-preconditioner workload, and the batched workload (20
+sources on 24^3 x 48, 16^4 and 8^4 solved together, against one at a time).
 """
 from __future__ import annotations
 
@@ -497,13 +497,15 @@ def learned_large(torch, gs, li):
     return out
 
 
-def batched_section(torch, gs, li, reps=2):
+def batched_section(torch, gs, li, reps=1):
     """The batched workload: 12 spin-colour point sources on 24^3 x 48
     (exp(i 0.2 H) seed 3, m0 = -0.35) plus 4 Gaussian sources on each of
     8^4 (seed 6) and 16^4 (seed 4), Type I, FP32 inner / FP64 outer, all in
-    one schur_solve_batched call (one persistent multi-source kernel per
-    lattice, the three lattices concurrently on their own streams); against
-    the same 20 solves one source at a time on one stream."""
+    one schur_solve_batched call (the 20 solves largest lattice first on four
+    concurrent lanes, each persistent kernel sized for its share of the GPU
+    at launch); against the same 20 solves one at a time on one stream.
+    Warm-up: one batched call to a loose tolerance (plans, stencil tuning,
+    lane contexts, workspaces)."""
     from lattice_inputs import torchgen
     specs = [("24^3x48 eps0.2", "point", 12), ("8^4 eps0.2", "gauss", 4), ("16^4 eps0.2", "gauss", 4)]
     m0 = -0.35
@@ -520,26 +522,34 @@ def batched_section(torch, gs, li, reps=2):
         ctxs.append(c)
         streams.append(s)
     o = gs.gs_default_opts(inner_prec=gs.GS_F32)
+    warm = gs.gs_default_opts(inner_prec=gs.GS_F32)
+    warm.tol = 1e-3
     torch.cuda.synchronize()
-    gs.schur_solve_batched(probs, o)          # warm-up (plans, tuning, workspaces)
+    gs.schur_solve_batched(probs, warm)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     worst, status = 0.0, gs.GS_OK
     for _ in range(reps):
+        for pr in probs:
+            pr["x"].zero_()
+        torch.cuda.synchronize()
         status, stats = gs.schur_solve_batched(probs, o)
         worst = max([worst] + [st.true_residual for st in stats])
     torch.cuda.synchronize()
     batched_s = (time.perf_counter() - t0) / reps
-    # the same solves one source at a time
-    t0 = time.perf_counter()
-    seq_worst = 0.0
-    for c, pr in zip(ctxs, probs):
+    # the same solves one source at a time, each lattice's total
+    seq_worst, per_lattice = 0.0, {}
+    for (name, _, _), c, pr in zip(specs, ctxs, probs):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         for j in range(pr["nrhs"]):
             st = gs.schur_solve(c.handle, 1, 0, 0, pr["f"][j], pr["x"][j], o)
             seq_worst = max(seq_worst, st.true_residual)
-    torch.cuda.synchronize()
-    seq_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        per_lattice[name] = round(time.perf_counter() - t1, 3)
+    seq_s = sum(per_lattice.values())
     nsol = sum(pr["nrhs"] for pr in probs)
+    lanes = ctxs[0].get_option(gs.GS_OPT_BATCH_LANES) or 4
     for c in ctxs:
         c.close()
     del probs
@@ -547,12 +557,12 @@ def batched_section(torch, gs, li, reps=2):
     return {"workload": "12 point sources on 24^3x48 (exp(i 0.2 H) seed 3) + 4 Gaussian sources on each of "
                         "8^4 (seed 6) and 16^4 (seed 4), Wilson m0=-0.35, Type I, outer GMRES(30) to 1e-10, "
                         "FP32 inner / FP64 outer",
-            "status": gs.STATUS_NAMES.get(status, status), "solves": nsol,
-            "site_rhs_per_stencil_sweep": 12 * 663552 + 4 * 4096 + 4 * 65536,
+            "status": gs.STATUS_NAMES.get(status, status), "solves": nsol, "lanes": lanes,
             "batched_s": batched_s, "value": nsol / batched_s, "unit": "solves/s",
             "max_true_residual": worst, "one_at_a_time_s": seq_s,
+            "one_at_a_time_s_per_lattice": per_lattice,
             "one_at_a_time_max_true_residual": seq_worst, "speedup": seq_s / batched_s,
-            "timing": "wall clock around the call (host threads per lattice), %d repetitions" % reps}
+            "timing": "wall clock around the call (host threads per lane), %d repetition(s)" % reps}
 
 
 def reusken_section(torch, gs, li, reps=20):
@@ -744,8 +754,8 @@ def main():
                     help="skip Table 1 on the GPU (plain / V-cycle BiCGStab on three 8^4 fields)")
     ap.add_argument("--no-mixed-large", action="store_true",
                     help="skip the 16^3x32 Type II mixed-precision solve")
-    ap.add_argument("--batched", action="store_true",
-                    help="add the batched multi-lattice multi-source section (about 6 minutes)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched multi-lattice multi-source section (about 2.5 minutes)")
     ap.add_argument("--only", default=None,
                     choices=["batched", "learned_large", "reusken", "table1", "mixed_large"],
                     help="run one section alone and print it")
@@ -1049,7 +1059,8 @@ def main():
                         "us_per_launch": r["us_per_launch"], "variant": r["variant"],
                         "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"]}
         line["dslash_lowp_32x32x32x64"] = lowp
-    if args.batched:
+    if not args.no_batched:
+        torch.cuda.empty_cache()
         line["batched"] = batched_section(torch, gs, li)
     if not args.no_learned:
         torch.cuda.empty_cache()

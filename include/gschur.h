@@ -144,7 +144,7 @@ gs_status gs_set_gauge(gs_ctx* ctx, const void* U_dev);
  * returns the forced value, or under autotuning the variant chosen most
  * recently. */
 enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 3, GS_OPT_MULTI_BATCH = 4,
-       GS_OPT_WAIT_LIMIT_US = 5, GS_OPT_COOP_BLOCKS = 6 };
+       GS_OPT_WAIT_LIMIT_US = 5, GS_OPT_COOP_BLOCKS = 6, GS_OPT_BATCH_LANES = 7 };
 /* GS_OPT_INNER_KERNEL: 0 = each inner BiCGStab solve runs as one persistent
  * cooperative kernel (grid barriers with bounded waits between its phases;
  * the default), 1 = five kernel launches per iteration with the convergence
@@ -165,10 +165,13 @@ enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 
  * kernels [1000000, i.e. 1 s].  A wait that runs out makes its kernel stop,
  * release what it holds (tensor memory) and report GS_TIMEOUT; the context
  * stays usable.
- * GS_OPT_COOP_BLOCKS: the number of blocks this context's persistent
- * (cooperative) solver kernels use while schur_solve_batched runs several
- * problems at once; 0 = the problem's share of the SMs, in proportion to its
- * V x nrhs (the default). */
+ * GS_OPT_COOP_BLOCKS: the number of blocks the persistent (cooperative)
+ * solver kernels of this problem use while schur_solve_batched runs several
+ * solves at once; 0 = sized at each launch for 1/n of the GPU while n solves
+ * run -- every co-resident block on rest sets above 16384 sites, two per SM
+ * below (the default).
+ * GS_OPT_BATCH_LANES (read from the first problem's context): how many solves
+ * schur_solve_batched runs at once, 1 .. 64; 0 = four (the default). */
 gs_status gs_set_option(gs_ctx* ctx, int option, int value);
 gs_status gs_get_option(gs_ctx* ctx, int option, int* value);
 
@@ -342,15 +345,24 @@ gs_status schur_solve_multi(gs_ctx* ctx, int type, int dir, int inverse, int nrh
                             gs_solve_stats* stats);
 
 /* Several problems -- lattices with their own contexts, permutations and
- * source counts -- solved concurrently, one host thread per problem: problem
- * i is schur_solve_multi on ctxs[i] (its own stream) with type[i], dir[i],
- * inverse[i], nrhs[i], f_dev[i], x_dev[i] -- or schur_solve when nrhs[i] is 1
- * (with plain FP64 inner solves, opts->inner_prec = GS_F64, every nrhs[i]
- * must be 1); each
- * problem's persistent kernels get a share of the SMs proportional to
- * V x nrhs (GS_OPT_COOP_BLOCKS overrides it per context).  The contexts must
- * be distinct (they may hold the same lattice and field).  stats (may be
- * NULL) is an array of nprob entries.  Returns the worst status. */
+ * source counts -- solved at once (Section 1 of the paper for each source).
+ * Problem i solves D x = f for the nrhs[i] sources f_dev[i] (complex128
+ * [nrhs[i]][V][4][3], site order) into x_dev[i] through S_bb of permutation
+ * (type[i], dir[i], inverse[i]) on the lattice of ctxs[i], with opts (any
+ * inner precision).  Every source is one schur_solve; the solves go largest
+ * lattice first to GS_OPT_BATCH_LANES concurrent lanes, each on a context of
+ * the source's lattice: the problem's own, or a lane context the library
+ * creates with its own stream and a copy of the problem's field (kept with
+ * the problem's context and released by gs_destroy; several GB on large
+ * lattices; its field is copied again after gs_set_gauge).  With the
+ * network inner solver (GS_INNER_FGMRES_NET) a problem's sources run on its
+ * own context only.  While n solves run, each persistent kernel takes 1/n
+ * of the GPU when launched (GS_OPT_COOP_BLOCKS).  The callers' streams are
+ * synchronised before the first solve, every lane stream before return.  The
+ * contexts must be distinct (they may hold the same lattice and field).
+ * stats (may be NULL): nprob entries, each aggregating its problem's sources
+ * (iterations summed, residuals the worst).  Returns the worst status; an
+ * error met on a lane context is reported on the problem's own. */
 gs_status schur_solve_batched(int nprob, gs_ctx* const* ctxs, const int* type, const int* dir,
                               const int* inverse, const int* nrhs, const void* const* f_dev,
                               void* const* x_dev, const gs_solve_opts* opts,

@@ -22,5 +22,5 @@ __all__ = ["Context", "GschurError", "gs_create", "gs_destroy", "gs_set_gauge",
            "GS_INNER_FGMRES_NET",
            "GS_TYPE_I", "GS_TYPE_II", "GS_F64", "GS_F32", "GS_BF16", "GS_GMRES",
            "GS_BICGSTAB", "GS_OK", "GS_MAXITER", "GS_BREAKDOWN", "STATUS_NAMES",
-           "schur_apply_reusken", "GS_OPT_MULTI_BATCH", "GS_OPT_WAIT_LIMIT_US", "GS_OPT_COOP_BLOCKS",
+           "schur_apply_reusken", "GS_OPT_MULTI_BATCH", "GS_OPT_WAIT_LIMIT_US", "GS_OPT_COOP_BLOCKS", "GS_OPT_BATCH_LANES",
            "gs_selftest_wait", "schur_apply_approx", "VCycle", "gs_solve_bicgstab"]

@@ -23,7 +23,7 @@ GS_F64, GS_F32, GS_BF16 = 0, 1, 2
 GS_GMRES, GS_BICGSTAB = 0, 1
 GS_INNER_BICGSTAB, GS_INNER_FGMRES_NET = 0, 1
 GS_OPT_STENCIL_VARIANT, GS_OPT_INNER_KERNEL, GS_OPT_NET_KERNEL, GS_OPT_MULTI_BATCH, \
-    GS_OPT_WAIT_LIMIT_US, GS_OPT_COOP_BLOCKS = 1, 2, 3, 4, 5, 6
+    GS_OPT_WAIT_LIMIT_US, GS_OPT_COOP_BLOCKS, GS_OPT_BATCH_LANES = 1, 2, 3, 4, 5, 6, 7
 GS_PROF_STENCIL_F64, GS_PROF_STENCIL_F32, GS_PROF_STENCIL_BF16, GS_PROF_SOLVER_F64, \
     GS_PROF_SOLVER_LP = range(5)
 

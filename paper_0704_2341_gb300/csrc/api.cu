@@ -128,6 +128,8 @@ gs_status gs_create(gs_ctx** out, const int dims[4], double m0, void* stream) {
 
 gs_status gs_destroy(gs_ctx* c) {
     if (!c) return GS_OK;
+    for (gs_ctx* l : c->lanes) gs_destroy(l);
+    c->lanes.clear();
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     free_multi(c);
@@ -176,6 +178,7 @@ gs_status gs_destroy(gs_ctx* c) {
     cudaFree(o.red.counter);
     if (o.hbuf_host) cudaFreeHost(o.hbuf_host);
     if (o.y_host) cudaFreeHost(o.y_host);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
     cudaGetLastError();
     delete c;
     return GS_OK;
@@ -207,6 +210,11 @@ gs_status gs_set_option(gs_ctx* c, int option, int value) {
     if (option == GS_OPT_COOP_BLOCKS) {
         if (value < 0 || value > 65536) return set_err(c, GS_EINVAL, "cooperative block count %d not in 0..65536", value);
         c->opt_coop_blocks = value;
+        return GS_OK;
+    }
+    if (option == GS_OPT_BATCH_LANES) {
+        if (value < 0 || value > 64) return set_err(c, GS_EINVAL, "batch lanes %d not in 0..64", value);
+        c->opt_batch_lanes = value;
         return GS_OK;
     }
     if (option == GS_OPT_WAIT_LIMIT_US) {
@@ -244,6 +252,10 @@ gs_status gs_get_option(gs_ctx* c, int option, int* value) {
         *value = c->opt_coop_blocks;
         return GS_OK;
     }
+    if (option == GS_OPT_BATCH_LANES) {
+        *value = c->opt_batch_lanes;
+        return GS_OK;
+    }
     return set_err(c, GS_EINVAL, "unknown option %d", option);
 }
 
@@ -277,6 +289,7 @@ gs_status gs_set_gauge(gs_ctx* c, const void* U_dev) {
     GS_CUDA(c, cudaMemcpyAsync(c->U_abi, U_dev, (size_t)c->V * 36 * sizeof(double2),
                                cudaMemcpyDeviceToDevice, c->stream));
     c->have_gauge = true;
+    c->gauge_gen++;
     c->net_links_fresh = false;
     invalidate_mixed_links(c);
     for (Plan* p : c->plans) {

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -209,6 +210,15 @@ struct gs_ctx {
     void* persist = nullptr;           // persistent-solver scratch (persistent.cu)
     void* multi = nullptr;             // multi-RHS workspaces (multi.cu)
     int coop_block_cap = 0;            // cap on cooperative grids (0 = whole GPU; batched solves)
+    // batched solves: the number of solves running at once, shared by the
+    // contexts of one schur_solve_batched call (null outside such a call);
+    // each cooperative grid takes its share of the GPU when it is launched
+    const std::atomic<int>* batch_running = nullptr;
+    int opt_batch_lanes = 0;           // concurrent solves of schur_solve_batched (0 = the library's choice)
+    std::vector<gs_ctx*> lanes;        // extra contexts on the same lattice for schur_solve_batched
+    cudaStream_t own_stream = nullptr; // a stream the library created for this context (lane contexts)
+    unsigned gauge_gen = 0;            // counts gs_set_gauge calls
+    unsigned lane_gauge_gen = 0;       // (lane contexts) the parent's gauge_gen their field was copied at
     struct gs_net* net = nullptr;      // learned preconditioner attached with gs_set_net (net.cu)
     bool net_links_fresh = false;      // the network's FP32 link copy matches U_abi
     float2 *fg_V = nullptr, *fg_Z = nullptr, *fg_w = nullptr;  // FGMRES-net vectors (FP32 stencil layout)
@@ -224,6 +234,30 @@ struct gs_ctx {
 };
 
 namespace gs {
+
+// largest rest set on which one source leaves the GPU latency bound (GB300:
+// sources that share launches win on 8^4, not from 16^4 up)
+constexpr int64_t kBatchMaxRestSites = 16384;
+
+// Blocks of a cooperative grid whose kernel fits per_sm blocks on an SM, for
+// a set of rest_sites sites: the whole GPU, or inside schur_solve_batched the
+// share of one of the solves running at that moment -- all co-resident
+// blocks on large sets (HBM bound: more loads in flight), two per SM on small
+// ones (latency bound: fewer, fuller blocks and cheaper barriers; measured on
+// 8^4: 76 blocks per solve beat 114 with four solves at once).  An explicit
+// cap (GS_OPT_COOP_BLOCKS in a batched call) takes precedence.
+inline int64_t coop_blocks(const gs_ctx* c, int per_sm, int64_t rest_sites) {
+    int64_t g = (int64_t)per_sm * c->num_sms;
+    if (c->coop_block_cap > 0) return g < c->coop_block_cap ? g : c->coop_block_cap;
+    if (c->batch_running) {
+        int n = c->batch_running->load(std::memory_order_relaxed);
+        if (n < 1) n = 1;
+        const int64_t per = (rest_sites <= kBatchMaxRestSites && per_sm > 2) ? 2 : per_sm;
+        g = per * c->num_sms / n;
+        if (g < 1) g = 1;
+    }
+    return g;
+}
 
 // error helpers --------------------------------------------------------------
 gs_status set_err(gs_ctx* c, gs_status s, const char* fmt, ...);

@@ -10,24 +10,15 @@
 // The inner D_rr solves of all sources run in one persistent cooperative
 // kernel with per-source BiCGStab scalars and convergence flags; the FP64
 // defect correction and the outer GMRES(m) run the sources in lock step
-// (one batched S_bb application per Arnoldi step).  schur_solve_batched runs
-// several such problems (different lattices) concurrently, one host thread
-// and stream per context, each persistent kernel limited to a share of the
-// SMs proportional to its work.
+// (one batched S_bb application per Arnoldi step).
 #include <math.h>
 
 #include <algorithm>
 #include <complex>
-#include <thread>
 #include <vector>
 
 #include "gridsync.cuh"
 #include "lowp.cuh"
-
-namespace gs {
-// largest rest set on which the sources of a problem share launches by default
-constexpr int64_t kBatchMaxRestSites = 16384;
-}  // namespace gs
 
 namespace gs {
 
@@ -682,8 +673,7 @@ static gs_status inner_solve_multi(gs_ctx* c, const Plan* p, int N, const double
                                   : k_bicg_persistent_multi<float>;
     GS_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, B, dsm));
     if (per_sm < 1) return set_err(c, GS_ECUDA, "multi-source kernel does not fit on an SM");
-    int64_t g = (int64_t)per_sm * c->num_sms;
-    if (c->coop_block_cap > 0 && g > c->coop_block_cap) g = c->coop_block_cap;
+    int64_t g = coop_blocks(c, per_sm, n);
     const int64_t want = (n + SB - 1) / SB;
     if (g > want) g = want < c->num_sms ? (want < 1 ? 1 : want) : want;
     if (g > (int64_t)per_sm * c->num_sms) g = (int64_t)per_sm * c->num_sms;
@@ -1300,61 +1290,6 @@ gs_status schur_solve_multi(gs_ctx* c, int type, int dir, int inverse, int nrhs,
     s = run();
     cudaStreamSynchronize(c->stream);
     return finish(s);
-}
-
-// Several problems (contexts) solved concurrently: one host thread each, on
-// each context's own stream; the persistent kernels of the problems share
-// the SMs in proportion to sites x sources.
-gs_status schur_solve_batched(int nprob, gs_ctx* const* ctxs, const int* type, const int* dir,
-                              const int* inverse, const int* nrhs, const void* const* f_dev,
-                              void* const* x_dev, const gs_solve_opts* opts, gs_solve_stats* stats) {
-    if (nprob < 1 || !ctxs || !type || !dir || !inverse || !nrhs || !f_dev || !x_dev) return GS_EINVAL;
-    double total = 0.0;
-    for (int i = 0; i < nprob; ++i) {
-        if (!ctxs[i]) return GS_EINVAL;
-        total += (double)ctxs[i]->V * nrhs[i];
-    }
-    std::vector<gs_status> res(nprob, GS_OK);
-    std::vector<gs_solve_stats> sts(nprob);
-    std::vector<int> caps(nprob);
-    for (int i = 0; i < nprob; ++i) {
-        gs_ctx* c = ctxs[i];
-        // blocks of 128..1024 threads: the cap is in blocks of the multi-source
-        // kernel, at least one block per SM share, at least 4
-        const double share = (double)c->V * nrhs[i] / total;
-        int cap = (int)(share * c->num_sms * 2.0 + 0.5);
-        caps[i] = cap < 4 ? 4 : cap;
-    }
-    // a problem of one source (and every problem with plain FP64 inner
-    // solves, which take one source) is the single-source schur_solve, its
-    // persistent solver kernels on its share
-    const bool f64 = opts && opts->inner_prec == GS_F64;
-    if (f64)
-        for (int i = 0; i < nprob; ++i)
-            if (nrhs[i] != 1)
-                return set_err(ctxs[i], GS_EINVAL, "schur_solve_batched with GS_F64 inner solves takes one "
-                                                   "source per problem (nrhs %d)", nrhs[i]);
-    std::vector<std::thread> th;
-    for (int i = 0; i < nprob; ++i) {
-        th.emplace_back([&, i]() {
-            gs_ctx* c = ctxs[i];
-            const int old = c->coop_block_cap;
-            c->coop_block_cap = nprob > 1 ? (c->opt_coop_blocks > 0 ? c->opt_coop_blocks : caps[i]) : old;
-            if (f64 || nrhs[i] == 1)
-                res[i] = schur_solve(c, type[i], dir[i], inverse[i], f_dev[i], x_dev[i], opts, &sts[i]);
-            else
-                res[i] = schur_solve_multi(c, type[i], dir[i], inverse[i], nrhs[i], f_dev[i], x_dev[i],
-                                           opts, &sts[i]);
-            c->coop_block_cap = old;
-        });
-    }
-    for (auto& t : th) t.join();
-    gs_status worst = GS_OK;
-    for (int i = 0; i < nprob; ++i) {
-        if (stats) stats[i] = sts[i];
-        if (res[i] != GS_OK && (worst == GS_OK || worst == GS_MAXITER)) worst = res[i];
-    }
-    return worst;
 }
 
 }  // extern "C"

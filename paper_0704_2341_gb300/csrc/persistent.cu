@@ -649,17 +649,17 @@ __global__ void __launch_bounds__(kPThreads) k_selftest_grid_timeout(GridSync g,
     grid_sync(g);
 }
 
-// co-resident grid for a cooperative launch: at most `want` blocks
+// co-resident grid for a cooperative launch on a set of rest_sites sites: at
+// most `want` blocks
 template <class K>
-static int coop_grid(gs_ctx* c, K kernel, int64_t want) {
+static int coop_grid(gs_ctx* c, K kernel, int64_t want, int64_t rest_sites) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPThreads, 0) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         return 0;
     }
-    int64_t g = (int64_t)per_sm * c->num_sms;
-    if (c->coop_block_cap > 0 && g > c->coop_block_cap) g = c->coop_block_cap;
+    int64_t g = coop_blocks(c, per_sm, rest_sites);
     if (want < g) g = want;
     if (g < 1) g = 1;
     if (g > kMaxRedBlocks) g = kMaxRedBlocks;
@@ -707,7 +707,7 @@ gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs
     if (s != GS_OK) return s;
     const int64_t tiles = (A.n_out + kSitesPerBlock - 1) / kSitesPerBlock;
     const int64_t want = tiles > (int64_t)c->num_sms ? tiles : (int64_t)c->num_sms;
-    const int g = coop_grid(c, k_bicg_persistent_f64, want);
+    const int g = coop_grid(c, k_bicg_persistent_f64, want, A.n_out);
     if (g < 1) return set_err(c, GS_ECUDA, "no co-resident grid for the persistent solver");
     // tiles of up to 32 sites, no more than the grid needs to cover the rest set
     // once (3840 sites on 152 blocks: 26 per tile, so every SM shares the work)
@@ -758,7 +758,7 @@ static gs_status persistent_bicg_lp_t(gs_ctx* c, const LpArgs& A, const LpArgs& 
     if (s != GS_OK) return s;
     const int64_t blocks = (n + kPThreads - 1) / kPThreads;
     const int64_t want = blocks > (int64_t)c->num_sms ? blocks : (int64_t)c->num_sms;
-    const int g = coop_grid(c, k_bicg_persistent_lp<S>, want);
+    const int g = coop_grid(c, k_bicg_persistent_lp<S>, want, n);
     if (g < 1) return set_err(c, GS_ECUDA, "no co-resident grid for the persistent solver");
     GS_CUDA(c, cudaMemsetAsync(ps->words, 0, 4 * sizeof(unsigned int), c->stream));
     PArgsLp P;

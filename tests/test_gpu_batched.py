@@ -1,6 +1,6 @@
 """Several sources and several lattices solved together (multi-source
 stencil, persistent multi-source inner solves, lock-step outer GMRES,
-concurrent batches), through the C ABI, against the FP64 oracle."""
+concurrent solves on lanes), through the C ABI, against the FP64 oracle."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as sla
@@ -192,8 +192,97 @@ def test_batched_plain_f64_four_permutations_match_one_at_a_time(env):
         x1 = torch.empty_like(f)
         c.schur_solve(t, mu, inv, f, x1, o)
         assert close(xb, x1.cpu().numpy(), 1e-8)
-    bad = [dict(p, nrhs=2) for p in probs[:2]]
-    status, _ = gs.schur_solve_batched(bad, o)
+    status, _ = gs.schur_solve_batched([probs[0], probs[0]], o)   # one context twice
+    assert status == gs.GS_EINVAL
+    status, _ = gs.schur_solve_batched([dict(probs[0], nrhs=0)], o)
     assert status == gs.GS_EINVAL
     for c in ctxs:
         c.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batched_sources_on_lane_contexts(env, prec):
+    """More sources than problems: the library spreads them over lane
+    contexts of the same lattice (its own streams and field copies); every
+    solution against a direct sparse solve, and the aggregated statistics
+    against the same sources solved one at a time."""
+    torch, gs = env
+    specs = [((4, 4, 4, 4), 0.2, 0.3, 0, 1, 0, 0, 5),
+             ((4, 2, 4, 4), -0.1, 0.3, 5, 2, 2, 1, 3)]
+    p = gs.GS_F64 if prec == "f64" else gs.GS_F32
+    o = gs.gs_default_opts(inner_prec=p)
+    ctxs, probs, refs, keep = [], [], [], []
+    for dims, m0, eps, seed, t, mu, inv, N in specs:
+        U = li.random_gauge(dims, eps, seed)
+        s = torch.cuda.Stream()
+        ctx = _ctx(gs, torch, dims, m0, U, s.cuda_stream)
+        f = li.gaussian_source(dims, seed + 70, n_src=N)
+        fd = to_dev(np.ascontiguousarray(f), torch)
+        probs.append(dict(ctx=ctx.handle, type=t, dir=mu, inverse=inv, nrhs=N, f=fd, x=torch.zeros_like(fd)))
+        refs.append((dirac.wilson_matrix(U, dims, m0).tocsc(), f))
+        ctxs.append(ctx)
+        keep.append(s)
+    ctxs[0].set_option(gs.GS_OPT_BATCH_LANES, 3)
+    assert ctxs[0].get_option(gs.GS_OPT_BATCH_LANES) == 3
+    torch.cuda.synchronize()
+    status, stats = gs.schur_solve_batched(probs, o)
+    assert status == gs.GS_OK
+    for (D, f), pr, st, c, spec in zip(refs, probs, stats, ctxs, specs):
+        t, mu, inv, N = spec[4:]
+        x = pr["x"].cpu().numpy().reshape(N, -1)
+        inner = 0
+        for j in range(N):
+            assert close(x[j], sla.spsolve(D, f[j].ravel()), 1e-9)
+            x1 = torch.zeros_like(pr["f"][j])
+            inner += c.schur_solve(t, mu, inv, pr["f"][j], x1, o).inner_solves
+        assert st.true_residual <= 1e-10
+        # the same work, up to an outer iteration or two where the grid sizes
+        # (and so the rounding of the reductions) differ
+        assert abs(st.inner_solves - inner) <= max(2 * N, inner // 10)
+    for c in ctxs:
+        c.close()
+
+
+def test_batched_lane_contexts_follow_a_new_field(env):
+    """Lane contexts keep a copy of the problem's field: after gs_set_gauge
+    on the problem's context the next batched call solves with the new one."""
+    torch, gs = env
+    dims, m0, N = (4, 4, 4, 4), 0.1, 4
+    U1, U2 = li.random_gauge(dims, 0.3, 11), li.random_gauge(dims, 0.4, 12)
+    ctx = _ctx(gs, torch, dims, m0, U1)
+    ctx.set_option(gs.GS_OPT_BATCH_LANES, 4)
+    f = li.gaussian_source(dims, 13, n_src=N)
+    fd = to_dev(np.ascontiguousarray(f), torch)
+    o = gs.gs_default_opts()
+    for U in (U1, U2):
+        ctx.set_gauge(to_dev(U, torch))
+        pr = dict(ctx=ctx.handle, type=1, dir=0, inverse=0, nrhs=N, f=fd, x=torch.zeros_like(fd))
+        status, (st,) = gs.schur_solve_batched([pr], o)
+        assert status == gs.GS_OK and st.true_residual <= 1e-10
+        D = dirac.wilson_matrix(U, dims, m0).tocsc()
+        x = pr["x"].cpu().numpy().reshape(N, -1)
+        for j in range(N):
+            assert close(x[j], sla.spsolve(D, f[j].ravel()), 1e-9)
+    with pytest.raises(gs.GschurError):
+        ctx.set_option(gs.GS_OPT_BATCH_LANES, 65)
+    ctx.close()
+
+
+def test_batched_one_lane_is_the_sequential_solve(env):
+    """GS_OPT_BATCH_LANES = 1: the sources one after another on the problem's
+    own context, with whole-GPU grids -- bit for bit the single-source calls."""
+    torch, gs = env
+    dims, m0, N = (4, 4, 4, 8), 0.0, 3
+    U = li.random_gauge(dims, 0.35, 21)
+    ctx = _ctx(gs, torch, dims, m0, U)
+    ctx.set_option(gs.GS_OPT_BATCH_LANES, 1)
+    fd = to_dev(np.ascontiguousarray(li.gaussian_source(dims, 22, n_src=N)), torch)
+    o = gs.gs_default_opts(inner_prec=gs.GS_F32)
+    pr = dict(ctx=ctx.handle, type=2, dir=3, inverse=0, nrhs=N, f=fd, x=torch.zeros_like(fd))
+    status, _ = gs.schur_solve_batched([pr], o)
+    assert status == gs.GS_OK
+    for j in range(N):
+        x1 = torch.zeros_like(fd[j])
+        ctx.schur_solve(2, 3, 0, fd[j], x1, o)
+        assert torch.equal(x1, pr["x"][j])
+    ctx.close()
