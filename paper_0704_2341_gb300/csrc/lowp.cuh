@@ -12,6 +12,19 @@ namespace gs {
 
 struct LpState;
 
+// The whole lattice in site order (x0 fastest), whose neighbours follow from
+// the site index: the stencil then reads no neighbour table.  k / L uses the
+// multiply-high method for division by an invariant integer (Granlund and
+// Montgomery, PLDI 1994): with l = ceil(log2 L) and
+// m = floor(2^32 (2^l - L) / L) + 1, k / L = (umulhi(k, m) + k) >> l for every
+// k < 2^31 (site indices are below 2^31 / 12).
+struct LexDims {
+    int on;         // 0: use the table
+    int L[4];
+    unsigned mag[3];
+    int sh[3];
+};
+
 // Arguments of the low-precision stencil launches (FP32 arithmetic).
 struct LpArgs {
     void* out;
@@ -26,6 +39,7 @@ struct LpArgs {
     float* partial;
     unsigned int* counter;
     int* ran;
+    LexDims lex;         // on: the set is the whole lattice in site order
 };
 
 namespace {
@@ -349,6 +363,56 @@ __device__ __forceinline__ float2 cmulf2(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+__device__ __forceinline__ unsigned lex_div(unsigned k, unsigned m, int l) {
+    return (__umulhi(k, m) + k) >> l;
+}
+
+// forward and backward neighbours of site k in direction mu, periodic
+__device__ __forceinline__ void lex_coords(const LexDims& d, int64_t k, int (&x)[4]) {
+    const unsigned s = (unsigned)k;
+    const unsigned q0 = lex_div(s, d.mag[0], d.sh[0]);
+    const unsigned q1 = lex_div(q0, d.mag[1], d.sh[1]);
+    const unsigned q2 = lex_div(q1, d.mag[2], d.sh[2]);
+    x[0] = (int)(s - q0 * (unsigned)d.L[0]);
+    x[1] = (int)(q0 - q1 * (unsigned)d.L[1]);
+    x[2] = (int)(q1 - q2 * (unsigned)d.L[2]);
+    x[3] = (int)q2;
+}
+
+template <int MU>
+__device__ __forceinline__ int2 lex_hop(const LexDims& d, int64_t k, const int (&x)[4]) {
+    int st = 1;
+#pragma unroll
+    for (int nu = 0; nu < MU; ++nu) st *= d.L[nu];
+    const int s = (int)k, L = d.L[MU];
+    return make_int2(x[MU] + 1 < L ? s + st : s - (L - 1) * st, x[MU] > 0 ? s - st : s + (L - 1) * st);
+}
+
+// the eight neighbours of site k: (f0, b0, f1, b1) and (f2, b2, f3, b3)
+__device__ __forceinline__ void site_nbrs(const LpArgs& a, int64_t k, int4& n01, int4& n23) {
+    if (a.lex.on) {
+        int x[4];
+        lex_coords(a.lex, k, x);
+        const int2 h0 = lex_hop<0>(a.lex, k, x), h1 = lex_hop<1>(a.lex, k, x);
+        const int2 h2 = lex_hop<2>(a.lex, k, x), h3 = lex_hop<3>(a.lex, k, x);
+        n01 = make_int4(h0.x, h0.y, h1.x, h1.y);
+        n23 = make_int4(h2.x, h2.y, h3.x, h3.y);
+    } else {
+        n01 = __ldg((const int4*)(a.nbr + k * 4));
+        n23 = __ldg((const int4*)(a.nbr + k * 4) + 1);
+    }
+}
+
+template <int MU>
+__device__ __forceinline__ int2 dir_nbr(const LpArgs& a, int64_t k) {
+    if (a.lex.on) {
+        int x[4];
+        lex_coords(a.lex, k, x);
+        return lex_hop<MU>(a.lex, k, x);
+    }
+    return __ldg(a.nbr + k * 4 + MU);
+}
+
 // ---------------------------------------------------------------------------
 // the low-precision stencil: a block of 4 warps covers 32 sites, warp w owns
 // direction mu = w (forward and backward hop) for all 32 sites.  All loads of
@@ -364,7 +428,7 @@ template <class S, int MU>
 __device__ __forceinline__ void lp_dir(const LpArgs& a, int64_t k, bool valid, float (&acc)[24]) {
 #pragma unroll
     for (int q = 0; q < 24; ++q) acc[q] = 0.f;
-    const int2 nb = valid ? __ldg(a.nbr + k * 4 + MU) : make_int2(-1, -1);
+    const int2 nb = valid ? dir_nbr<MU>(a, k) : make_int2(-1, -1);
     const bool hf = nb.x >= 0, hb = nb.y >= 0;
     const int64_t jf = hf ? nb.x : 0, jb = hb ? nb.y : 0, jk = valid ? k : 0;
     float pf[24], pb[24], lf[12], lb[12];
@@ -585,8 +649,8 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_lp_pipe(LpArgs a) {
     float e[3] = {0.f, 0.f, 0.f};
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        const int4 n01 = __ldg((const int4*)(a.nbr + k * 4));
-        const int4 n23 = __ldg((const int4*)(a.nbr + k * 4) + 1);
+        int4 n01, n23;
+        site_nbrs(a, k, n01, n23);
         // out-of-set neighbours (-1) read the site itself and are masked
         const bool h0f = n01.x >= 0, h0b = n01.y >= 0, h1f = n01.z >= 0, h1b = n01.w >= 0;
         const bool h2f = n23.x >= 0, h2b = n23.y >= 0, h3f = n23.z >= 0, h3b = n23.w >= 0;
@@ -642,8 +706,8 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_lp_site(LpArgs a) {
     float e[3] = {0.f, 0.f, 0.f};
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        const int4 n01 = __ldg((const int4*)(a.nbr + k * 4));
-        const int4 n23 = __ldg((const int4*)(a.nbr + k * 4) + 1);
+        int4 n01, n23;
+        site_nbrs(a, k, n01, n23);
         float acc[24];
 #pragma unroll
         for (int q = 0; q < 24; ++q) acc[q] = 0.f;

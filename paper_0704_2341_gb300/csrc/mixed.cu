@@ -357,6 +357,7 @@ struct LpPlanData {
                            // site with the next direction's loads in flight (3/4 blocks)
     int2* nbr_r = nullptr;
     void* links = nullptr;
+    LexDims lex{};         // the whole lattice: neighbours by arithmetic (identity plan)
 };
 
 static size_t spinor_bytes(int prec) { return prec == GS_BF16 ? 48 : 96; }
@@ -461,6 +462,7 @@ static gs_status lp_tune(gs_ctx* c, LpPlanData& pd) {
     a.in = m->w.p;
     a.links = pd.links;
     a.nbr = pd.nbr_r;
+    a.lex = pd.lex;
     a.n = pd.n;
     a.diag = (float)(c->m0 + 4.0);
     a.epi = EPI_NONE;
@@ -496,6 +498,23 @@ static gs_status lp_tune(gs_ctx* c, LpPlanData& pd) {
     return s;
 }
 
+// neighbour arithmetic of the whole lattice (LexDims): extents and the
+// multiply-high constants of L0, L1, L2
+static LexDims lex_dims(const int dims[4]) {
+    LexDims d;
+    memset(&d, 0, sizeof d);
+    d.on = 1;
+    for (int mu = 0; mu < 4; ++mu) d.L[mu] = dims[mu];
+    for (int i = 0; i < 3; ++i) {
+        const unsigned long long L = (unsigned long long)dims[i];
+        int l = 0;
+        while ((1ull << l) < L) ++l;
+        d.sh[i] = l;
+        d.mag[i] = (unsigned)((((1ull << 32) * ((1ull << l) - L)) / L) + 1ull);
+    }
+    return d;
+}
+
 static gs_status lp_plan(gs_ctx* c, const Plan* p, int prec, LpPlanData** out) {
     MixedState* m = mixed_of(c);
     for (auto& pd : m->plans)
@@ -510,6 +529,7 @@ static gs_status lp_plan(gs_ctx* c, const Plan* p, int prec, LpPlanData** out) {
     pd.nb = (p->type == 0) ? 0 : p->nb;
     pd.n = c->V - pd.nb;
     pd.hops = (p->type == 0) ? p->hops[0][0] : p->hops[1][1];
+    if (p->type == 0) pd.lex = lex_dims(c->dims);
     const int64_t n = pd.n;
     if (cudaMalloc(&pd.nbr_r, (size_t)n * 4 * sizeof(int2)) != cudaSuccess ||
         cudaMalloc(&pd.links, (size_t)n * 4 * link_bytes(prec)) != cudaSuccess) {
@@ -568,6 +588,7 @@ static gs_status lp_bicgstab(gs_ctx* c, LpPlanData* pd, int64_t n, float tol, in
     k1.in = w.p;
     k1.links = pd->links;
     k1.nbr = pd->nbr_r;
+    k1.lex = pd->lex;
     k1.n = n;
     k1.diag = (float)(c->m0 + 4.0);
     k1.epi = EPI_DOT_RHAT_V;
@@ -705,6 +726,7 @@ gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2*
             A.in = w.p;
             A.links = pd->links;
             A.nbr = pd->nbr_r;
+            A.lex = pd->lex;
             A.n = n;
             A.diag = (float)(c->m0 + 4.0);
             A.epi = EPI_DOT_RHAT_V;
@@ -850,6 +872,7 @@ gs_status lp_rr_apply_f32(gs_ctx* c, const Plan* p, const void* x, void* y) {
     a.in = x;
     a.links = pd->links;
     a.nbr = pd->nbr_r;
+    a.lex = pd->lex;
     a.n = pd->n;
     a.diag = (float)(c->m0 + 4.0);
     a.epi = EPI_NONE;
@@ -910,6 +933,7 @@ gs_status wilson_apply_lowp(gs_ctx* c, int type, int dir, int inverse, int prec,
     a.in = x_lp_dev;
     a.links = pd->links;
     a.nbr = pd->nbr_r;
+    a.lex = pd->lex;
     a.n = pd->n;
     a.diag = (float)(c->m0 + 4.0);
     a.epi = EPI_NONE;

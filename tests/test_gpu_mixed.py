@@ -126,11 +126,13 @@ def test_lowp_tol_validation(env):
 
 @pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("prec,tol", [("f32", 4e-6), ("bf16", 3e-2)])
-@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (3, 4, 2, 5)])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (3, 4, 2, 5), (12, 10, 6, 14)])
 def test_lowp_stencil_full_lattice(env, prec, tol, dims, variant):
     """wilson_apply_lowp (type 0, whole lattice) against the oracle's D in
     FP64, to the rounding of the storage format (FP32: 2^-24, BF16: 2^-9 per
-    input, about 100 terms per output)."""
+    input, about 100 terms per output).  On the whole lattice the kernels
+    compute the neighbours from the site index (odd extents, L = 2 and a
+    10080-site lattice over many blocks check that arithmetic)."""
     torch, gs = env
     U = li.random_gauge(dims, 0.4, 3)
     ctx = _ctx(gs, torch, dims, -0.2, U)
