@@ -131,7 +131,30 @@ __device__ __forceinline__ void gather(unsigned char* base, int bi, int j, const
 // (backward hop; the link is the neighbour's).  Warp items = (8 sites) x
 // (8 input rows); lane = (site j, row q) handles rows q and q + 4 of its
 // site with the link loaded once; the bf16x2 stores of a warp land in 32
-// distinct banks (bank = 4 (row mod 8) + q).
+// distinct banks (bank = 4 (row mod 8) + q).  Each output colour is one FMA
+// chain per real component; the three rows' core-matrix offsets are computed
+// once per item and the row bounds are checked only on the tile's edge items.
+__device__ __forceinline__ uint32_t core_row(int r) { return (uint32_t)((r >> 3) * kSBO + (r & 7) * 16); }
+
+// t = sum_c m_c p_c  (m_c = U[a][c]: forward) or sum_c conj(m_c) p_c (backward)
+template <bool CONJ>
+__device__ __forceinline__ float2 row3(float2 m0, float2 m1, float2 m2, float2 p0, float2 p1, float2 p2) {
+    const float s = CONJ ? -1.f : 1.f;
+    float re = m0.x * p0.x;
+    re = fmaf(-s * m0.y, p0.y, re);
+    re = fmaf(m1.x, p1.x, re);
+    re = fmaf(-s * m1.y, p1.y, re);
+    re = fmaf(m2.x, p2.x, re);
+    re = fmaf(-s * m2.y, p2.y, re);
+    float im = m0.x * p0.y;
+    im = fmaf(s * m0.y, p0.x, im);
+    im = fmaf(m1.x, p1.y, im);
+    im = fmaf(s * m1.y, p1.x, im);
+    im = fmaf(m2.x, p2.y, im);
+    im = fmaf(s * m2.y, p2.x, im);
+    return make_float2(re, im);
+}
+
 template <int MODE>
 __device__ __forceinline__ void stage_chunk(const unsigned char* P, const float2* Ub, unsigned char* a_s, int warp,
                                             int sj, int kq, int off, int nsite) {
@@ -141,6 +164,9 @@ __device__ __forceinline__ void stage_chunk(const unsigned char* P, const float2
         const int r0 = 3 * sl - off;
         if (r0 >= kRows) continue;
         const bool have = sl < nsite;
+        const bool edge = r0 < 0 || r0 + 2 >= kRows;
+        const uint32_t o0 = r0 >= 0 ? core_row(r0) : 0u, o1 = r0 + 1 >= 0 ? core_row(r0 + 1) : 0u,
+                       o2 = core_row(r0 + 2 < kRows ? r0 + 2 : kRows - 1);
         float2 u[9];
         if (MODE != 0 && have) {
 #pragma unroll
@@ -149,34 +175,36 @@ __device__ __forceinline__ void stage_chunk(const unsigned char* P, const float2
 #pragma unroll
         for (int h2 = 0; h2 < 2; ++h2) {
             const int kk = 8 * kg + 4 * h2 + kq;
-            float2 t[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            // core matrix column of k' = 2 kk: (2 kk / 8) * 128 + (2 kk % 8) * 2
+            const uint32_t ok = (uint32_t)((2 * kg + h2) * 128 + 4 * kq);
+            float2 t0 = make_float2(0.f, 0.f), t1 = t0, t2 = t0;
             if (have) {
                 const __nv_bfloat162* pr = (const __nv_bfloat162*)(P + sl * kPStride) + kk * 3;
                 const float2 p0 = __bfloat1622float2(pr[0]), p1 = __bfloat1622float2(pr[1]),
                              p2 = __bfloat1622float2(pr[2]);
                 if (MODE == 0) {
-                    t[0] = p0;
-                    t[1] = p1;
-                    t[2] = p2;
+                    t0 = p0;
+                    t1 = p1;
+                    t2 = p2;
                 } else if (MODE == 1) {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const float2 q0 = cmul(u[3 * a], p0), q1 = cmul(u[3 * a + 1], p1), q2 = cmul(u[3 * a + 2], p2);
-                        t[a] = make_float2(q0.x + q1.x + q2.x, q0.y + q1.y + q2.y);
-                    }
+                    t0 = row3<false>(u[0], u[1], u[2], p0, p1, p2);
+                    t1 = row3<false>(u[3], u[4], u[5], p0, p1, p2);
+                    t2 = row3<false>(u[6], u[7], u[8], p0, p1, p2);
                 } else {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const float2 q0 = cmulc(u[a], p0), q1 = cmulc(u[3 + a], p1), q2 = cmulc(u[6 + a], p2);
-                        t[a] = make_float2(q0.x + q1.x + q2.x, q0.y + q1.y + q2.y);
-                    }
+                    t0 = row3<true>(u[0], u[3], u[6], p0, p1, p2);
+                    t1 = row3<true>(u[1], u[4], u[7], p0, p1, p2);
+                    t2 = row3<true>(u[2], u[5], u[8], p0, p1, p2);
                 }
             }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int r = r0 + a;
-                if (r >= 0 && r < kRows)
-                    *(__nv_bfloat162*)(a_s + core_off(r, 2 * kk)) = __floats2bfloat162_rn(t[a].x, t[a].y);
+            if (!edge) {
+                *(__nv_bfloat162*)(a_s + o0 + ok) = __floats2bfloat162_rn(t0.x, t0.y);
+                *(__nv_bfloat162*)(a_s + o1 + ok) = __floats2bfloat162_rn(t1.x, t1.y);
+                *(__nv_bfloat162*)(a_s + o2 + ok) = __floats2bfloat162_rn(t2.x, t2.y);
+            } else {
+                if (r0 >= 0) *(__nv_bfloat162*)(a_s + o0 + ok) = __floats2bfloat162_rn(t0.x, t0.y);
+                if (r0 + 1 >= 0 && r0 + 1 < kRows)
+                    *(__nv_bfloat162*)(a_s + o1 + ok) = __floats2bfloat162_rn(t1.x, t1.y);
+                if (r0 + 2 < kRows) *(__nv_bfloat162*)(a_s + o2 + ok) = __floats2bfloat162_rn(t2.x, t2.y);
             }
         }
     }
@@ -237,10 +265,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else {
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
             }
-            __syncthreads();
             const uint32_t s = g & 1u, u = g >> 1;
-            if (g >= 2 && !mbar_wait(su32(&mdone[s]), (u - 1) & 1u, wait_ns)) bad = 1;
-            if (tid == 0 && !bad) {
+            // the MMAs of chunk g - 2 read this A stage: one thread waits for
+            // their commit, the block barrier passes the news on
+            if (tid == 0 && g >= 2 && !mbar_wait(su32(&mdone[s]), (u - 1) & 1u, wait_ns)) bad = 1;
+            if (__syncthreads_or(bad)) {
+                bad = 1;
+                break;
+            }
+            if (tid == 0) {
                 const uint32_t bar = su32(&bfull[s]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBBytes)
                              : "memory");
