@@ -16,14 +16,18 @@
 // (leading byte offset), 8-row groups 768 bytes apart (stride byte offset).
 // The input activations are BF16 ([V][96][3] complex as bf16x2).
 //
-// Pipeline per chunk j of a tile: cp.async gathers the raw neighbour rows and
-// links of chunk j + 1 (double-buffered) while the threads transport chunk j
-// into the A stage (double-buffered, reused once the tensor core has
-// committed the chunk two back; a thread handles two input rows of one site); one thread moves B_j by a bulk copy and,
-// after the block barrier, issues the chunk's six MMAs and commits them to
-// the stage's mbarrier.  Every wait is bounded (the context's wait limit,
-// GS_OPT_WAIT_LIMIT_US, 1 s by default); on a
-// timeout the kernel stops, frees its tensor memory and raises err.
+// Warp roles.  Warps 0-14 gather and transport: at chunk j they gather the
+// raw neighbour rows of chunk j + 2 by cp.async (three raw buffers; the links
+// of a transport once, two link buffers by transport parity), transport
+// chunk j into the A stage (two stages, reused once the tensor core has
+// committed the chunk two back) and arrive on the stage's full barrier; one
+// named barrier per chunk among these warps orders the raw buffers.  Warp 15
+// moves B_j by a bulk copy and issues the chunk's six MMAs as soon as the
+// stage is full, then commits them to the stage's done barrier, so the MMAs
+// never wait for a block barrier.  Every wait is bounded (the context's wait
+// limit, GS_OPT_WAIT_LIMIT_US, 1 s by default); on a timeout the kernel
+// stops, waits (bounded) for the MMAs it committed, frees its tensor memory
+// and raises err.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -45,11 +49,16 @@ constexpr uint32_t kBBytes = kN * kKC * 2;       // 18432
 constexpr uint32_t kPStride = kQ * 3 * 4 + 16;   // 304: raw rows of one site (+16 against bank conflicts)
 constexpr uint32_t kPBytes = kSites * kPStride;  // 26752
 constexpr uint32_t kUBytes = kSites * 9 * 8;     // 6336
-// dynamic shared memory map (offsets from a 128-byte aligned base)
-constexpr uint32_t kOffA = 0, kOffB = 2 * kABytes, kOffP = kOffB + 2 * kBBytes, kOffU = kOffP + 2 * kPBytes,
+// dynamic shared memory map (offsets from a 128-byte aligned base): A and B
+// stages x 2, raw rows x 3, links x 2, neighbour table
+constexpr uint32_t kOffA = 0, kOffB = 2 * kABytes, kOffP = kOffB + 2 * kBBytes, kOffU = kOffP + 3 * kPBytes,
                    kOffY = kOffU + 2 * kUBytes, kSmemUsed = kOffY + 9 * kSites * 4;
 constexpr size_t kSmem = kSmemUsed + 128;
 constexpr int kThreads = 512;
+constexpr int kStageWarps = 15;                  // gather + transport; warp 15 issues B and the MMAs
+constexpr int kStageThreads = kStageWarps * 32;
+constexpr int kHalfItems = 11 * 3 * 2;           // (8 site slots) x (8 rows) x (first / second row of a lane)
+static_assert(kSmem <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint64_t gtime() {
@@ -103,21 +112,23 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(a) b
     return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 
-// raw rows (and links) of chunk j of the tile into raw buffer bi
-__device__ __forceinline__ void gather(unsigned char* base, int bi, int j, const __nv_bfloat162* __restrict__ in,
+// raw rows of chunk j of the tile into raw buffer j % 3, and with the first
+// quarter of a transport its links into link buffer (transport & 1); issued
+// by the transport warps, one commit group per chunk
+__device__ __forceinline__ void gather(unsigned char* base, int j, const __nv_bfloat162* __restrict__ in,
                                        const float2* __restrict__ U32, int64_t xs0, int nsite) {
     const int d = j >> 2, qt = j & 3;
     const int* Y = (const int*)(base + kOffY) + d * kSites;
-    const uint32_t P = su32(base + kOffP + bi * kPBytes);
-    for (int i = threadIdx.x; i < nsite * 18; i += kThreads) {
+    const uint32_t P = su32(base + kOffP + (j % 3) * kPBytes);
+    for (int i = threadIdx.x; i < nsite * 18; i += kStageThreads) {
         const int sl = i / 18, pc = i - sl * 18;
         const unsigned char* src = (const unsigned char*)(in + ((int64_t)Y[sl] * kRC + kQ * qt) * 3) + pc * 16;
         cp_async16(P + sl * kPStride + pc * 16, src);
     }
-    if (d > 0 && qt < 2) {  // links of transport d (quarters 2, 3 reuse buffers 0, 1)
+    if (d > 0 && qt == 0) {  // links of transport d, kept for its four quarters
         const int mu = (d - 1) & 3;
-        const uint32_t Ub = su32(base + kOffU + bi * kUBytes);
-        for (int i = threadIdx.x; i < nsite * 9; i += kThreads) {
+        const uint32_t Ub = su32(base + kOffU + (d & 1) * kUBytes);
+        for (int i = threadIdx.x; i < nsite * 9; i += kStageThreads) {
             const int sl = i / 9, e = i - sl * 9;
             const int64_t ls = d <= 4 ? xs0 + sl : (int64_t)Y[sl];
             cp_async8(Ub + (sl * 9 + e) * 8, U32 + (ls * 4 + mu) * 9 + e);
@@ -128,12 +139,13 @@ __device__ __forceinline__ void gather(unsigned char* base, int bi, int j, const
 
 // Transport one chunk (24 input rows) of the raw rows in shared memory into
 // the A stage.  MODE 0: identity, 1: U_mu(x) p (forward hop), 2: U^dag p
-// (backward hop; the link is the neighbour's).  Warp items = (8 sites) x
-// (8 input rows); lane = (site j, row q) handles rows q and q + 4 of its
-// site with the link loaded once; the bf16x2 stores of a warp land in 32
-// distinct banks (bank = 4 (row mod 8) + q).  Each output colour is one FMA
-// chain per real component; the three rows' core-matrix offsets are computed
-// once per item and the row bounds are checked only on the tile's edge items.
+// (backward hop; the link is the neighbour's).  Half-items = (8 site slots)
+// x (8 input rows) x (first or second row of a lane): lane = (site j, row q)
+// handles row q or q + 4 of its site; the 66 half-items go in contiguous runs
+// of four or five to the 15 transport warps, so a warp loads a site's link at
+// most twice.  The bf16x2 stores of a warp land in 32 distinct banks (bank =
+// 4 (row mod 8) + q).  Each output colour is one FMA chain per real
+// component; the row bounds are checked only on the tile's edge items.
 __device__ __forceinline__ uint32_t core_row(int r) { return (uint32_t)((r >> 3) * kSBO + (r & 7) * 16); }
 
 // t = sum_c m_c p_c  (m_c = U[a][c]: forward) or sum_c conj(m_c) p_c (backward)
@@ -158,56 +170,65 @@ __device__ __forceinline__ float2 row3(float2 m0, float2 m1, float2 m2, float2 p
 template <int MODE>
 __device__ __forceinline__ void stage_chunk(const unsigned char* P, const float2* Ub, unsigned char* a_s, int warp,
                                             int sj, int kq, int off, int nsite) {
-    for (int wi = warp; wi < 11 * 3; wi += kThreads / 32) {
-        const int sg = wi / 3, kg = wi - sg * 3;
+    const int h0 = warp * kHalfItems / kStageWarps, h1 = (warp + 1) * kHalfItems / kStageWarps;
+    int cached = -1;
+    float2 u[9];
+    for (int hi = h0; hi < h1; ++hi) {
+        const int sg = hi / 6, rem = hi - 6 * sg, kg = rem >> 1, h2 = rem & 1;
         const int sl = 8 * sg + sj;
         const int r0 = 3 * sl - off;
         if (r0 >= kRows) continue;
         const bool have = sl < nsite;
-        const bool edge = r0 < 0 || r0 + 2 >= kRows;
-        const uint32_t o0 = r0 >= 0 ? core_row(r0) : 0u, o1 = r0 + 1 >= 0 ? core_row(r0 + 1) : 0u,
-                       o2 = core_row(r0 + 2 < kRows ? r0 + 2 : kRows - 1);
-        float2 u[9];
-        if (MODE != 0 && have) {
+        if (MODE != 0 && have && sg != cached) {
 #pragma unroll
             for (int e = 0; e < 9; ++e) u[e] = Ub[sl * 9 + e];
+            cached = sg;
         }
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            const int kk = 8 * kg + 4 * h2 + kq;
-            // core matrix column of k' = 2 kk: (2 kk / 8) * 128 + (2 kk % 8) * 2
-            const uint32_t ok = (uint32_t)((2 * kg + h2) * 128 + 4 * kq);
-            float2 t0 = make_float2(0.f, 0.f), t1 = t0, t2 = t0;
-            if (have) {
-                const __nv_bfloat162* pr = (const __nv_bfloat162*)(P + sl * kPStride) + kk * 3;
-                const float2 p0 = __bfloat1622float2(pr[0]), p1 = __bfloat1622float2(pr[1]),
-                             p2 = __bfloat1622float2(pr[2]);
-                if (MODE == 0) {
-                    t0 = p0;
-                    t1 = p1;
-                    t2 = p2;
-                } else if (MODE == 1) {
-                    t0 = row3<false>(u[0], u[1], u[2], p0, p1, p2);
-                    t1 = row3<false>(u[3], u[4], u[5], p0, p1, p2);
-                    t2 = row3<false>(u[6], u[7], u[8], p0, p1, p2);
-                } else {
-                    t0 = row3<true>(u[0], u[3], u[6], p0, p1, p2);
-                    t1 = row3<true>(u[1], u[4], u[7], p0, p1, p2);
-                    t2 = row3<true>(u[2], u[5], u[8], p0, p1, p2);
-                }
-            }
-            if (!edge) {
-                *(__nv_bfloat162*)(a_s + o0 + ok) = __floats2bfloat162_rn(t0.x, t0.y);
-                *(__nv_bfloat162*)(a_s + o1 + ok) = __floats2bfloat162_rn(t1.x, t1.y);
-                *(__nv_bfloat162*)(a_s + o2 + ok) = __floats2bfloat162_rn(t2.x, t2.y);
+        const int kk = 8 * kg + 4 * h2 + kq;
+        // core matrix column of k' = 2 kk: (2 kk / 8) * 128 + (2 kk % 8) * 2
+        const uint32_t ok = (uint32_t)((2 * kg + h2) * 128 + 4 * kq);
+        float2 t0 = make_float2(0.f, 0.f), t1 = t0, t2 = t0;
+        if (have) {
+            const __nv_bfloat162* pr = (const __nv_bfloat162*)(P + sl * kPStride) + kk * 3;
+            const float2 p0 = __bfloat1622float2(pr[0]), p1 = __bfloat1622float2(pr[1]),
+                         p2 = __bfloat1622float2(pr[2]);
+            if (MODE == 0) {
+                t0 = p0;
+                t1 = p1;
+                t2 = p2;
+            } else if (MODE == 1) {
+                t0 = row3<false>(u[0], u[1], u[2], p0, p1, p2);
+                t1 = row3<false>(u[3], u[4], u[5], p0, p1, p2);
+                t2 = row3<false>(u[6], u[7], u[8], p0, p1, p2);
             } else {
-                if (r0 >= 0) *(__nv_bfloat162*)(a_s + o0 + ok) = __floats2bfloat162_rn(t0.x, t0.y);
-                if (r0 + 1 >= 0 && r0 + 1 < kRows)
-                    *(__nv_bfloat162*)(a_s + o1 + ok) = __floats2bfloat162_rn(t1.x, t1.y);
-                if (r0 + 2 < kRows) *(__nv_bfloat162*)(a_s + o2 + ok) = __floats2bfloat162_rn(t2.x, t2.y);
+                t0 = row3<true>(u[0], u[3], u[6], p0, p1, p2);
+                t1 = row3<true>(u[1], u[4], u[7], p0, p1, p2);
+                t2 = row3<true>(u[2], u[5], u[8], p0, p1, p2);
             }
+        }
+        if (r0 >= 0 && r0 + 2 < kRows) {
+            *(__nv_bfloat162*)(a_s + core_row(r0) + ok) = __floats2bfloat162_rn(t0.x, t0.y);
+            *(__nv_bfloat162*)(a_s + core_row(r0 + 1) + ok) = __floats2bfloat162_rn(t1.x, t1.y);
+            *(__nv_bfloat162*)(a_s + core_row(r0 + 2) + ok) = __floats2bfloat162_rn(t2.x, t2.y);
+        } else {
+            if (r0 >= 0) *(__nv_bfloat162*)(a_s + core_row(r0) + ok) = __floats2bfloat162_rn(t0.x, t0.y);
+            if (r0 + 1 >= 0 && r0 + 1 < kRows)
+                *(__nv_bfloat162*)(a_s + core_row(r0 + 1) + ok) = __floats2bfloat162_rn(t1.x, t1.y);
+            if (r0 + 2 < kRows) *(__nv_bfloat162*)(a_s + core_row(r0 + 2) + ok) = __floats2bfloat162_rn(t2.x, t2.y);
         }
     }
+}
+
+// named barrier of the transport warps with an OR of v over them
+__device__ __forceinline__ bool stage_sync_or(int v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(v), "n"(kStageThreads)
+        : "memory");
+    return r != 0;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -216,14 +237,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                   const int2* __restrict__ nbr, int64_t V, int* err, unsigned long long wait_ns) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    __shared__ __align__(8) uint64_t bfull[2], mdone[2];
+    // afull: the transport warps filled A stage s; bfull: B_j landed in B stage
+    // s; mdone: the MMAs of the stage's chunk completed (tcgen05.commit)
+    __shared__ __align__(8) uint64_t afull[2], bfull[2], mdone[2];
     __shared__ uint32_t tslot;
+    __shared__ uint32_t committed;   // chunks whose MMAs warp 15 has committed
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&afull[s])), "r"(kStageWarps));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bfull[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mdone[s])));
         }
+        committed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
@@ -237,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int64_t rows = 3 * V;
     const int64_t ntiles = (rows + kRows - 1) / kRows;
-    uint32_t g = 0;  // chunks issued so far (stage = g & 1, use = g >> 1)
+    uint32_t g = 0;  // chunks of the tiles before this one (stage = g & 1, use = g >> 1)
     int bad = 0;
     const int kq = lane & 3, sj = lane >> 2;
     for (int64_t tile = blockIdx.x; tile < ntiles && !bad; tile += gridDim.x) {
@@ -257,23 +283,42 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncthreads();
-        gather(base, 0, 0, in, U32, xs0, nsite);
-        for (int j = 0; j < kChunks; ++j, ++g) {
-            if (j + 1 < kChunks) {
-                gather(base, (j + 1) & 1, j + 1, in, U32, xs0, nsite);
-                asm volatile("cp.async.wait_group 1;" ::: "memory");
-            } else {
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (warp < kStageWarps) {
+            gather(base, 0, in, U32, xs0, nsite);
+            gather(base, 1, in, U32, xs0, nsite);
+            for (int j = 0; j < kChunks; ++j) {
+                const uint32_t gj = g + (uint32_t)j, s = gj & 1u, u = gj >> 1;
+                if (j + 1 < kChunks) asm volatile("cp.async.wait_group 1;" ::: "memory");
+                else asm volatile("cp.async.wait_group 0;" ::: "memory");
+                // the MMAs of chunk gj - 2 read this A stage: one thread waits
+                // for their commit, the named barrier passes the news on (and
+                // that every transport warp is done with chunk j - 1's raw rows)
+                if (tid == 0 && gj >= 2 && !mbar_wait(su32(&mdone[s]), (u - 1) & 1u, wait_ns)) bad = 1;
+                if (stage_sync_or(bad)) {
+                    bad = 1;
+                    break;
+                }
+                if (j + 2 < kChunks) gather(base, j + 2, in, U32, xs0, nsite);
+                const int d = j >> 2;
+                const unsigned char* P = base + kOffP + (j % 3) * kPBytes;
+                const float2* Ub = (const float2*)(base + kOffU + (d & 1) * kUBytes);
+                unsigned char* a_s = base + kOffA + s * kABytes;
+                if (d == 0) stage_chunk<0>(P, Ub, a_s, warp, sj, kq, off, nsite);
+                else if (d <= 4) stage_chunk<1>(P, Ub, a_s, warp, sj, kq, off, nsite);
+                else stage_chunk<2>(P, Ub, a_s, warp, sj, kq, off, nsite);
+                // the tensor core reads the stage through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&afull[s])) : "memory");
             }
-            const uint32_t s = g & 1u, u = g >> 1;
-            // the MMAs of chunk g - 2 read this A stage: one thread waits for
-            // their commit, the block barrier passes the news on
-            if (tid == 0 && g >= 2 && !mbar_wait(su32(&mdone[s]), (u - 1) & 1u, wait_ns)) bad = 1;
-            if (__syncthreads_or(bad)) {
-                bad = 1;
-                break;
-            }
-            if (tid == 0) {
+        } else if (lane == 0) {
+            // warp 15: B_j by bulk copy, then the chunk's MMAs once A and B are in
+            for (int j = 0; j < kChunks; ++j) {
+                const uint32_t gj = g + (uint32_t)j, s = gj & 1u, u = gj >> 1;
+                if (gj >= 2 && !mbar_wait(su32(&mdone[s]), (u - 1) & 1u, wait_ns)) {  // B stage s free
+                    bad = 1;
+                    break;
+                }
                 const uint32_t bar = su32(&bfull[s]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBBytes)
                              : "memory");
@@ -282,53 +327,41 @@ __global__ void __launch_bounds__(kThreads, 1)
                         su32(base + kOffB + s * kBBytes)),
                     "l"(Bw + (size_t)j * (kBBytes / 2)), "r"(kBBytes), "r"(bar)
                     : "memory");
-            }
-            // transport chunk j into the A stage
-            const int d = j >> 2, bi = j & 1;
-            const unsigned char* P = base + kOffP + bi * kPBytes;
-            const float2* Ub = (const float2*)(base + kOffU + bi * kUBytes);
-            unsigned char* a_s = base + kOffA + s * kABytes;
-            if (d == 0) stage_chunk<0>(P, Ub, a_s, warp, sj, kq, off, nsite);
-            else if (d <= 4) stage_chunk<1>(P, Ub, a_s, warp, sj, kq, off, nsite);
-            else stage_chunk<2>(P, Ub, a_s, warp, sj, kq, off, nsite);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (__syncthreads_or(bad)) {
-                bad = 1;
-                break;
-            }
-            if (tid == 0) {
-                if (!mbar_wait(su32(&bfull[s]), u & 1u, wait_ns)) {
+                if (!mbar_wait(su32(&afull[s]), u & 1u, wait_ns) || !mbar_wait(bar, u & 1u, wait_ns)) {
                     bad = 1;
-                } else {
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t a0 = su32(base + kOffA + s * kABytes), b0 = su32(base + kOffB + s * kBBytes);
-#pragma unroll
-                    for (int q = 0; q < 2; ++q)
-#pragma unroll
-                        for (int ks = 0; ks < kKC / 16; ++ks) {
-                            const uint64_t ad = sdesc(a0 + q * 16 * kSBO + ks * 256);
-                            const uint64_t bd = sdesc(b0 + ks * 256);
-                            const uint32_t acc = (j > 0 || ks > 0) ? 1u : 0u;
-                            asm volatile(
-                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-                                    tmem + (uint32_t)(q * kN)),
-                                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
-                                : "memory");
-                        }
-                    asm volatile(
-                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                            su32(&mdone[s]))
-                        : "memory");
+                    break;
                 }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t a0 = su32(base + kOffA + s * kABytes), b0 = su32(base + kOffB + s * kBBytes);
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int ks = 0; ks < kKC / 16; ++ks) {
+                        const uint64_t ad = sdesc(a0 + q * 16 * kSBO + ks * 256);
+                        const uint64_t bd = sdesc(b0 + ks * 256);
+                        const uint32_t acc = (j > 0 || ks > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                tmem + (uint32_t)(q * kN)),
+                            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                            : "memory");
+                    }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        su32(&mdone[s]))
+                    : "memory");
+                committed = gj + 1;
             }
         }
-        if (bad) break;
+        __syncwarp();
         // epilogue: the last chunk's commit covers every MMA of the tile
-        {
-            const uint32_t gl = g - 1, s = gl & 1u, u = gl >> 1;
-            if (!mbar_wait(su32(&mdone[s]), u & 1u, wait_ns)) bad = 1;
+        if (tid == 0 && !bad) {
+            const uint32_t gl = g + kChunks - 1;
+            if (!mbar_wait(su32(&mdone[gl & 1u]), (gl >> 1) & 1u, wait_ns)) bad = 1;
         }
+        g += kChunks;
+        if (__syncthreads_or(bad)) bad = 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!bad) {
             // warp w reads lanes 32 (w % 4) .. + 31 of accumulator (w / 4) % 2, columns half w / 8
@@ -364,8 +397,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (bad && tid == 0) atomicExch(err, 1);
     // every committed MMA has been waited for on the normal path; after a
     // timeout give the in-flight ones a bounded time before freeing
-    if (bad && tid == 0 && g > 0) {
-        const uint32_t gl = g - 1;
+    __syncthreads();
+    if (bad && tid == 0 && committed > 0) {
+        const uint32_t gl = committed - 1;
         mbar_wait(su32(&mdone[gl & 1u]), (gl >> 1) & 1u, wait_ns);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
