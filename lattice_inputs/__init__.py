@@ -166,7 +166,105 @@ def ape_smear(U, dims, alpha, steps) -> np.ndarray:
 
 # ---------------------------------------------------------------------------
 # plaquette-action pseudo-heatbath
+#
+# A heatbath chain amplifies the last bit of any rounding difference into a
+# different configuration after a few hundred sweeps, so every step below
+# uses only IEEE-754 operations that are correctly rounded on every machine
+# (+, -, x, /, sqrt on float64 arrays, one operation per numpy call, and
+# frexp): no BLAS products, no library log / cos, no SVD.  The same seed gives
+# the same field bit for bit on x86 and on Arm.
 # ---------------------------------------------------------------------------
+
+def _cmm(A, B):
+    """Complex matrix product A @ B for stacks (..., n, k) x (..., k, m) in
+    real arithmetic with a fixed summation order."""
+    Ar, Ai, Br, Bi = A.real, A.imag, B.real, B.imag
+    Cr = Ar[..., :, 0:1] * Br[..., 0:1, :]
+    Cr = Cr - Ai[..., :, 0:1] * Bi[..., 0:1, :]
+    Ci = Ar[..., :, 0:1] * Bi[..., 0:1, :]
+    Ci = Ci + Ai[..., :, 0:1] * Br[..., 0:1, :]
+    for j in range(1, A.shape[-1]):
+        Cr = Cr + Ar[..., :, j:j + 1] * Br[..., j:j + 1, :]
+        Cr = Cr - Ai[..., :, j:j + 1] * Bi[..., j:j + 1, :]
+        Ci = Ci + Ar[..., :, j:j + 1] * Bi[..., j:j + 1, :]
+        Ci = Ci + Ai[..., :, j:j + 1] * Br[..., j:j + 1, :]
+    C = np.empty(Cr.shape, dtype=np.complex128)
+    C.real = Cr
+    C.imag = Ci
+    return C
+
+
+def _reunitarize(M):
+    """SU(3) from the first two rows of each 3 x 3 matrix: Gram-Schmidt, then
+    row 3 = conj(row 1 x row 2) (determinant 1 by construction)."""
+    ur, ui = M[..., 0, :].real.copy(), M[..., 0, :].imag.copy()
+    vr, vi = M[..., 1, :].real.copy(), M[..., 1, :].imag.copy()
+    n = np.sqrt(ur[..., 0] * ur[..., 0] + ui[..., 0] * ui[..., 0] + ur[..., 1] * ur[..., 1]
+                + ui[..., 1] * ui[..., 1] + ur[..., 2] * ur[..., 2] + ui[..., 2] * ui[..., 2])
+    ur = ur / n[..., None]
+    ui = ui / n[..., None]
+    # <u, v> = sum conj(u_i) v_i
+    pr = ur[..., 0] * vr[..., 0] + ui[..., 0] * vi[..., 0]
+    pi = ur[..., 0] * vi[..., 0] - ui[..., 0] * vr[..., 0]
+    for i in (1, 2):
+        pr = pr + ur[..., i] * vr[..., i]
+        pr = pr + ui[..., i] * vi[..., i]
+        pi = pi + ur[..., i] * vi[..., i]
+        pi = pi - ui[..., i] * vr[..., i]
+    vr = vr - (pr[..., None] * ur - pi[..., None] * ui)
+    vi = vi - (pr[..., None] * ui + pi[..., None] * ur)
+    n = np.sqrt(vr[..., 0] * vr[..., 0] + vi[..., 0] * vi[..., 0] + vr[..., 1] * vr[..., 1]
+                + vi[..., 1] * vi[..., 1] + vr[..., 2] * vr[..., 2] + vi[..., 2] * vi[..., 2])
+    vr = vr / n[..., None]
+    vi = vi / n[..., None]
+    out = np.empty(M.shape, dtype=np.complex128)
+    out[..., 0, :].real, out[..., 0, :].imag = ur, ui
+    out[..., 1, :].real, out[..., 1, :].imag = vr, vi
+    for c, (a, b) in enumerate(((1, 2), (2, 0), (0, 1))):
+        # (u x v)_c = u_a v_b - u_b v_a; row 3 is its complex conjugate
+        xr = (ur[..., a] * vr[..., b] - ui[..., a] * vi[..., b]) - (ur[..., b] * vr[..., a] - ui[..., b] * vi[..., a])
+        xi = (ur[..., a] * vi[..., b] + ui[..., a] * vr[..., b]) - (ur[..., b] * vi[..., a] + ui[..., b] * vr[..., a])
+        out[..., 2, c].real = xr
+        out[..., 2, c].imag = -xi
+    return out
+
+
+_LN2 = 0.6931471805599453
+
+
+def _log(x):
+    """Natural logarithm of positive float64 values: x = m 2^e exactly
+    (frexp), m moved into [1/sqrt 2, sqrt 2), log m = 2 atanh(s) with
+    s = (m - 1) / (m + 1), |s| < 0.172, summed as the odd series to s^25
+    (error below 1e-17 relative to log m)."""
+    m, e = np.frexp(x)
+    low = m < 0.7071067811865476
+    m = np.where(low, m * 2.0, m)
+    e = np.where(low, e - 1, e).astype(np.float64)
+    s = (m - 1.0) / (m + 1.0)
+    s2 = s * s
+    acc = np.full_like(s, 1.0 / 25.0)
+    for k in range(23, 0, -2):
+        acc = acc * s2 + 1.0 / k
+    return e * _LN2 + 2.0 * s * acc
+
+
+def _unit_circle(n, rng):
+    """n points (c, s) uniform on the unit circle, by rejection from the square."""
+    c = np.empty(n)
+    s = np.empty(n)
+    todo = np.arange(n)
+    while todo.size:
+        x = 2.0 * rng.random(todo.size) - 1.0
+        y = 2.0 * rng.random(todo.size) - 1.0
+        r2 = x * x + y * y
+        ok = (r2 <= 1.0) & (r2 > 1e-12)
+        r = np.sqrt(r2[ok])
+        c[todo[ok]] = x[ok] / r
+        s[todo[ok]] = y[ok] / r
+        todo = todo[~ok]
+    return c, s
+
 
 def _staple_sum(G, mu):
     """A_mu(x) with Re tr(U_mu(x) A_mu(x)) = sum of the 6 plaquettes through the link."""
@@ -177,25 +275,27 @@ def _staple_sum(G, mu):
             continue
         Un = G[..., nu, :, :]
         # forward: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-        A += _shift(Un, mu, 1) @ _dag(_shift(Um, nu, 1)) @ _dag(Un)
+        A = A + _cmm(_cmm(_shift(Un, mu, 1), _dag(_shift(Um, nu, 1))), _dag(Un))
         # backward: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
         Un_m = _shift(Un, nu, -1)
-        A += _dag(_shift(Un_m, mu, 1)) @ _dag(_shift(Um, nu, -1)) @ Un_m
+        A = A + _cmm(_cmm(_dag(_shift(Un_m, mu, 1)), _dag(_shift(Um, nu, -1))), Un_m)
     return A
 
 
 def _kp_sample_x0(alpha, rng):
-    """Kennedy-Pendleton: x0 in [-1, 1] with density ~ sqrt(1 - x0^2) exp(alpha x0)."""
+    """Kennedy-Pendleton: x0 in [-1, 1] with density ~ sqrt(1 - x0^2) exp(alpha x0).
+    cos^2 of a uniform angle is the squared first coordinate of a uniform
+    point on the unit circle."""
     n = alpha.shape[0]
     out = np.empty(n)
     todo = np.arange(n)
     while todo.size:
         a = alpha[todo]
         r1 = 1.0 - rng.random(todo.size)
-        r2 = rng.random(todo.size)
+        c, _ = _unit_circle(todo.size, rng)
         r3 = 1.0 - rng.random(todo.size)
         r4 = rng.random(todo.size)
-        delta = -(np.log(r1) + np.cos(2.0 * np.pi * r2) ** 2 * np.log(r3)) / a
+        delta = -(_log(r1) + (c * c) * _log(r3)) / a
         ok = r4 * r4 <= 1.0 - 0.5 * delta
         out[todo[ok]] = 1.0 - delta[ok]
         todo = todo[~ok]
@@ -208,7 +308,7 @@ def _su2_heatbath_update(Ulinks, A, beta, rng, sub):
     Ulinks, A: (n, 3, 3).  Returns the updated links.
     """
     i, j = sub
-    W = Ulinks @ A
+    W = _cmm(Ulinks, A)
     w00, w01, w10, w11 = W[:, i, i], W[:, i, j], W[:, j, i], W[:, j, j]
     a0 = 0.5 * (w00 + w11).real
     a3 = 0.5 * (w00 - w11).imag
@@ -220,10 +320,10 @@ def _su2_heatbath_update(Ulinks, A, beta, rng, sub):
     # uniform direction for the remaining three components
     rad = np.sqrt(np.maximum(0.0, 1.0 - x0 * x0))
     cth = 2.0 * rng.random(x0.shape[0]) - 1.0
-    phi = 2.0 * np.pi * rng.random(x0.shape[0])
+    cph, sph = _unit_circle(x0.shape[0], rng)
     sth = np.sqrt(1.0 - cth * cth)
-    x1 = rad * sth * np.cos(phi)
-    x2 = rad * sth * np.sin(phi)
+    x1 = rad * sth * cph
+    x2 = rad * sth * sph
     x3 = rad * cth
     # quaternion product x * what^dagger, what = (a0, a1, a2, a3)/k
     b0, b1, b2, b3 = a0 / k, -a1 / k, -a2 / k, -a3 / k
@@ -233,13 +333,13 @@ def _su2_heatbath_update(Ulinks, A, beta, rng, sub):
     r3 = x0 * b3 + x3 * b0 - x1 * b2 + x2 * b1
     # embedded 2x2: r0 + i (r1 s1 + r2 s2 + r3 s3)
     R = np.empty((x0.shape[0], 2, 2), dtype=np.complex128)
-    R[:, 0, 0] = r0 + 1j * r3
-    R[:, 0, 1] = r2 + 1j * r1
-    R[:, 1, 0] = -r2 + 1j * r1
-    R[:, 1, 1] = r0 - 1j * r3
+    R[:, 0, 0].real, R[:, 0, 0].imag = r0, r3
+    R[:, 0, 1].real, R[:, 0, 1].imag = r2, r1
+    R[:, 1, 0].real, R[:, 1, 0].imag = -r2, r1
+    R[:, 1, 1].real, R[:, 1, 1].imag = r0, -r3
     rows = Ulinks[:, [i, j], :]
     out = Ulinks.copy()
-    out[:, [i, j], :] = R @ rows
+    out[:, [i, j], :] = _cmm(R, rows)
     return out
 
 
@@ -250,7 +350,9 @@ def heatbath_gauge(dims, beta, sweeps, seed, start=None) -> np.ndarray:
     mu = 0..3 and, for each mu, the even then the odd sites (checkerboard:
     links of one direction on one parity share no staple), and performs the
     three Cabibbo-Marinari subgroup updates (0,1), (1,2), (0,2).  All L_mu
-    must be even.  Random numbers come from ``numpy.random.default_rng(seed)``.
+    must be even.  Random numbers come from ``numpy.random.default_rng(seed)``;
+    only correctly rounded float64 operations act on them, so the field is the
+    same bit for bit on every machine.
     """
     if any(int(L) % 2 for L in dims):
         raise ValueError("heatbath checkerboard needs even extents")
@@ -276,7 +378,7 @@ def heatbath_gauge(dims, beta, sweeps, seed, start=None) -> np.ndarray:
                 Gm[sel] = links
                 G[..., mu, :, :] = Gm
         # keep the links unitary against rounding drift
-        G = _project_su3(G)
+        G = _reunitarize(G)
     return np.ascontiguousarray(G.reshape(V, 4, 3, 3))
 
 
@@ -322,13 +424,18 @@ def point_sources(dims, site=0) -> np.ndarray:
 # on-disk cache for the slow generators (a convenience; never required)
 # ---------------------------------------------------------------------------
 
+# bumped whenever a generator's output changes, so that no stale field is read
+# (2: the heatbath in correctly rounded arithmetic only)
+_CACHE_VERSION = 2
+
+
 def _cache_path(name):
     import os
     root = os.environ.get("GSCHUR_FIELD_CACHE")
     if root is None:
         root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                             ".cache", "fields")
-    return os.path.join(root, name + ".npy")
+    return os.path.join(root, "%s.v%d.npy" % (name, _CACHE_VERSION))
 
 
 def cached(name, make):

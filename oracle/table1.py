@@ -87,6 +87,7 @@ def run_field(U, dims, m0, levels, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_
                         "R": krylov.convergence_rate(info["history"]),
                         "R_arith": krylov.mean_ratio(info["history"]),
                         "residual": float(np.linalg.norm(D @ x - f) / np.linalg.norm(f)),
+                        "history": [float(h) for h in info["history"]],
                         "seconds": time.time() - t0}
     t0 = time.time()
     vc = vcycle.VCycle(D, dims, levels, schur=schur, inner=inner_tol,
@@ -96,6 +97,7 @@ def run_field(U, dims, m0, levels, tol=1e-8, inner_tol=1e-2, maxiter=3000, seed_
                              "iters": info["iters"], "converged": info["converged"], "R": info["R"],
                              "R_arith": krylov.mean_ratio(info["history"]),
                              "residual": float(np.linalg.norm(D @ x - f) / np.linalg.norm(f)),
+                             "history": [float(h) for h in info["history"]],
                              "inner_solves": len(vc.inner_log),
                              "inner_steps_max": max((s for _, s, _ in vc.inner_log), default=0),
                              "inner_not_converged": sum(1 for *_, c in vc.inner_log if not c),

@@ -136,9 +136,20 @@ def _check(out, res, true_res):
     for name, (st, R, hist) in res.items():
         o = out[name]
         assert o["converged"] and st.status == 0
-        # one step; on long plain runs (hundreds of steps of a non-monotone
-        # recursion) rounding order shifts the count by a few per cent
-        slack = max(1, int(round(0.03 * o["iters"])))
+        if name == "plain":
+            # the same iterates: the relative residual histories coincide over
+            # the first 20 steps, where the GPU's and the oracle's rounding
+            # orders have not yet pulled them apart (the V-cycle's rest-set
+            # solves stop at 1e-2, so its histories agree less closely)
+            g = np.asarray(hist) / hist[0]
+            h = np.asarray(o["history"]) / o["history"][0]
+            k = min(20, len(g), len(h))
+            assert np.abs(g[:k] - h[:k]).max() <= 1e-6 * np.abs(h[:k]).max(), (name, g[:k], h[:k])
+        # the step count: one step on short runs; a long BiCGStab run (a
+        # non-monotone recursion over hundreds of steps) ends a few per cent
+        # earlier or later once rounding has moved the iterates, and Section 4
+        # of the paper reports its rate R, checked to 0.02
+        slack = max(1, int(round((0.05 if o["iters"] >= 100 else 0.03) * o["iters"])))
         assert abs(st.outer_iters - o["iters"]) <= slack, (name, st.outer_iters, o["iters"])
         assert abs(R - o["R"]) <= 0.02, (name, R, o["R"])
         assert len(hist) == st.outer_iters + 1

@@ -44,6 +44,37 @@ def test_heatbath_limits():
     assert abs(li.average_plaquette(U, d2) - (1 - 2 / 30.0)) < 0.01
 
 
+def test_heatbath_is_the_same_on_every_machine():
+    """The heatbath chain turns a last-bit rounding difference into another
+    configuration, so it uses correctly rounded float64 operations only: this
+    4^4 field has the same bytes on x86-64 and on aarch64 (the digest was
+    taken on both)."""
+    import hashlib
+    U = li.heatbath_gauge((4, 4, 4, 4), 5.4, 10, 3)
+    assert _su3_ok(U)
+    digest = hashlib.sha256(np.ascontiguousarray(U).tobytes()).hexdigest()
+    assert digest == "bbfa43e5a479a2d7dbd2badd41e4f748a4d3a782a575a19ef70ad061d85339d5"
+
+
+def test_library_helpers_of_the_heatbath():
+    """The correctly rounded helpers against numpy / LAPACK: complex products,
+    the SU(3) re-unitarisation, the logarithm, points on the circle."""
+    rng = np.random.default_rng(5)
+    A = rng.normal(size=(40, 3, 3)) + 1j * rng.normal(size=(40, 3, 3))
+    B = rng.normal(size=(40, 3, 2)) + 1j * rng.normal(size=(40, 3, 2))
+    assert np.abs(li._cmm(A, B) - A @ B).max() < 1e-13
+    W = li._reunitarize(A)
+    assert np.abs(W @ np.conj(np.swapaxes(W, -1, -2)) - np.eye(3)).max() < 1e-14
+    assert np.abs(np.linalg.det(W) - 1).max() < 1e-14
+    # Gram-Schmidt: the first row is the normalised first row of the input
+    assert np.abs(W[:, 0] - A[:, 0] / np.linalg.norm(A[:, 0], axis=1)[:, None]).max() < 1e-15
+    x = np.concatenate([rng.random(1000) * 5 + 1e-300, np.exp(rng.uniform(-700, 700, 1000))])
+    assert np.abs(li._log(x) - np.log(x)).max() < 1e-12
+    c, s = li._unit_circle(5000, rng)
+    assert np.abs(c * c + s * s - 1).max() < 1e-15
+    assert abs(np.mean(c * c) - 0.5) < 0.02 and abs(np.mean(c)) < 0.03
+
+
 def test_sources():
     d = (2, 2, 2, 2)
     s = li.gaussian_source(d, 100)
