@@ -282,6 +282,32 @@ def _staple_sum(G, mu):
     return A
 
 
+def _nbr_tables(dims):
+    """Flat site indices of x + mu and x - mu for every site, per direction
+    (site order: x0 fastest), periodic."""
+    L0, L1, L2, L3 = dims
+    idx = np.arange(volume(dims)).reshape(L3, L2, L1, L0)
+    fwd = [np.roll(idx, -1, axis=3 - mu).ravel() for mu in range(4)]
+    bwd = [np.roll(idx, 1, axis=3 - mu).ravel() for mu in range(4)]
+    return fwd, bwd
+
+
+def _staple_sites(Gf, mu, S, fwd, bwd):
+    """_staple_sum restricted to the sites S (flat indices; Gf: (V, 4, 3, 3)),
+    term for term in the same order, so its values equal those of the whole-
+    lattice sum at those sites bit for bit."""
+    A = np.zeros((S.size, 3, 3), dtype=np.complex128)
+    xm = fwd[mu][S]
+    for nu in range(4):
+        if nu == mu:
+            continue
+        xn, xb = fwd[nu][S], bwd[nu][S]
+        A = A + _cmm(_cmm(Gf[xm, nu], _dag(Gf[xn, mu])), _dag(Gf[S, nu]))
+        xmb = bwd[nu][xm]
+        A = A + _cmm(_cmm(_dag(Gf[xmb, nu]), _dag(Gf[xb, mu])), Gf[xb, nu])
+    return A
+
+
 def _kp_sample_x0(alpha, rng):
     """Kennedy-Pendleton: x0 in [-1, 1] with density ~ sqrt(1 - x0^2) exp(alpha x0).
     cos^2 of a uniform angle is the squared first coordinate of a uniform
@@ -363,23 +389,22 @@ def heatbath_gauge(dims, beta, sweeps, seed, start=None) -> np.ndarray:
                             (V, 4, 3, 3)).copy()
     else:
         G = np.array(start, dtype=np.complex128, copy=True)
-    G = _to_grid(G, dims)
-    par = _parity_mask(dims)
+    G = np.ascontiguousarray(G.reshape(V, 4, 3, 3))
+    par = _parity_mask(dims).ravel()
+    sites = [np.flatnonzero(par == p) for p in (0, 1)]
+    fwd, bwd = _nbr_tables(dims)
     for _ in range(int(sweeps)):
         for mu in range(4):
             for p in (0, 1):
-                A = _staple_sum(G, mu)
-                sel = par == p
-                links = G[..., mu, :, :][sel]
-                As = A[sel]
+                S = sites[p]
+                As = _staple_sites(G, mu, S, fwd, bwd)
+                links = G[S, mu]
                 for sub in ((0, 1), (1, 2), (0, 2)):
                     links = _su2_heatbath_update(links, As, beta, rng, sub)
-                Gm = G[..., mu, :, :]
-                Gm[sel] = links
-                G[..., mu, :, :] = Gm
+                G[S, mu] = links
         # keep the links unitary against rounding drift
         G = _reunitarize(G)
-    return np.ascontiguousarray(G.reshape(V, 4, 3, 3))
+    return G
 
 
 def average_plaquette(U, dims) -> float:

@@ -56,6 +56,35 @@ def test_heatbath_is_the_same_on_every_machine():
     assert digest == "bbfa43e5a479a2d7dbd2badd41e4f748a4d3a782a575a19ef70ad061d85339d5"
 
 
+def test_staples_on_a_parity_equal_the_whole_lattice_sum():
+    """The heatbath computes the staples of one parity's links only; they are
+    the whole-lattice staple sum at those sites, bit for bit, and the staple
+    closes the plaquettes: Re tr(U_mu(x) A_mu(x)) summed over x is twice the
+    sum over x of the plaquettes in the planes (mu, nu != mu)."""
+    d = (4, 2, 4, 2)
+    U = li.random_gauge(d, 0.4, 8)
+    G = li._to_grid(U, d)
+    fwd, bwd = li._nbr_tables(d)
+    par = li._parity_mask(d).ravel()
+    for mu in range(4):
+        full = li._staple_sum(G, mu).reshape(-1, 3, 3)
+        for p in (0, 1):
+            S = np.flatnonzero(par == p)
+            part = li._staple_sites(U, mu, S, fwd, bwd)
+            assert np.array_equal(part, full[S])
+    mu = 1
+    A = li._staple_sum(G, mu).reshape(-1, 3, 3)
+    lhs = np.einsum("xab,xba->", U[:, mu], A).real
+    rhs = 0.0
+    for nu in range(4):
+        if nu == mu:
+            continue
+        Um, Un = G[..., mu, :, :], G[..., nu, :, :]
+        P = Um @ li._shift(Un, mu, 1) @ li._dag(li._shift(Um, nu, 1)) @ li._dag(Un)
+        rhs += 2.0 * np.trace(P, axis1=-2, axis2=-1).real.sum()
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs)
+
+
 def test_library_helpers_of_the_heatbath():
     """The correctly rounded helpers against numpy / LAPACK: complex products,
     the SU(3) re-unitarisation, the logarithm, points on the circle."""
