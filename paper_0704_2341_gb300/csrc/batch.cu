@@ -12,12 +12,13 @@
 // at ~0.6 of HBM bandwidth and spends the rest waiting at its grid barriers;
 // a few solves side by side fill those gaps (24^3 x 48, FP32 inner: 5.87 s per
 // solve alone, 5.49 / 5.31 / 5.26 / 5.32 s with 2 / 3 / 4 / 6 at once, so four
-// lanes by default).  While n solves run, each cooperative grid is sized at
-// launch for 1/n of the GPU (coop_blocks), so the blocks a finished solve
-// frees go to the next inner solves of the others; every persistent solver
-// kernel has the same block footprint (128 threads, 168 registers), which
-// keeps the shares co-resident.
+// lanes by default).  The cooperative grids of the running solves are drawn
+// from one block ledger (BlockLedger): every persistent solver kernel has the
+// same block footprint (128 threads, 168 registers), a grid is granted only
+// from blocks no other solve holds, so all of them stay co-resident, and the
+// blocks a finished solve frees go to the next launches of the others.
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
 #include <mutex>
 #include <thread>
@@ -94,6 +95,67 @@ gs_status worse(gs_status a, gs_status b) {
 
 }  // namespace
 
+namespace gs {
+
+void ledger_enter(BlockLedger* L, const gs_ctx* c) {
+    std::lock_guard<std::mutex> lk(L->mu);
+    L->held.push_back({c, 0, false});
+    L->running.fetch_add(1);
+}
+
+void ledger_leave(BlockLedger* L, const gs_ctx* c) {
+    {
+        std::lock_guard<std::mutex> lk(L->mu);
+        for (size_t k = 0; k < L->held.size(); ++k)
+            if (L->held[k].ctx == c) {
+                L->held.erase(L->held.begin() + (long)k);
+                break;
+            }
+        L->running.fetch_sub(1);
+    }
+    L->cv.notify_all();
+}
+
+int64_t ledger_grant(gs_ctx* c, int per_sm, int64_t want, int64_t target) {
+    BlockLedger* L = c->ledger;
+    const int64_t capacity = (int64_t)per_sm * c->num_sms;
+    int64_t limit = want < target ? want : target;
+    if (limit < 1) limit = 1;
+    std::unique_lock<std::mutex> lk(L->mu);
+    BlockLedger::Entry* mine = nullptr;
+    for (auto& e : L->held)
+        if (e.ctx == c) mine = &e;
+    if (!mine) return 0;
+    const auto t0 = std::chrono::steady_clock::now();
+    const auto bound = std::chrono::nanoseconds((long long)(c->wait_ns > 0 ? c->wait_ns : 1000000000ull) * 60);
+    for (;;) {
+        // held: blocks that may be in flight now; claimed: the same with
+        // every solve that has not launched yet counted at the reserve
+        int64_t held = 0, claimed = 0;
+        for (const auto& e : L->held)
+            if (e.ctx != c) {
+                held += e.blocks;
+                claimed += e.launched ? e.blocks : (e.blocks > L->reserve ? e.blocks : L->reserve);
+            }
+        int64_t g = limit < capacity - claimed ? limit : capacity - claimed;
+        if (g < 1) g = limit < capacity - held ? limit : capacity - held;
+        if (g >= 1) {
+            mine->blocks = g;
+            mine->launched = true;
+            L->cv.notify_all();   // a solve waiting for blocks may find some now
+            return g;
+        }
+        // every block is held by the others' kernels in flight: one of them
+        // ends or shrinks at its next launch
+        if (std::chrono::steady_clock::now() - t0 > bound) return 0;
+        L->cv.wait_for(lk, std::chrono::milliseconds(1));
+        for (auto& e : L->held)
+            if (e.ctx == c) mine = &e;
+    }
+}
+
+}  // namespace gs
+
 extern "C" {
 
 gs_status schur_solve_batched(int nprob, gs_ctx* const* ctxs, const int* type, const int* dir,
@@ -137,7 +199,10 @@ gs_status schur_solve_batched(int nprob, gs_ctx* const* ctxs, const int* type, c
     std::vector<gs_solve_stats> sts(nprob);
     for (auto& s : sts) memset(&s, 0, sizeof s);
     std::vector<std::string> msg(nprob);
-    std::atomic<int> running{0};
+    BlockLedger ledger;
+    // a solve that has not launched yet is counted at a third of an even
+    // share of the co-resident blocks (one block per SM share at 3 per SM)
+    ledger.reserve = std::max(1, ctxs[0]->num_sms / std::max(1, lanes));
     size_t left = items.size();
 
     auto lane = [&]() {
@@ -164,7 +229,6 @@ gs_status schur_solve_batched(int nprob, gs_ctx* const* ctxs, const int* type, c
                 taken[it] = 1;
                 --left;
                 busy[items[it].prob][slot] = 1;
-                running.fetch_add(1);
             }
             const int i = items[it].prob, j = items[it].src;
             gs_ctx* c = ctxs[i];
@@ -180,20 +244,25 @@ gs_status schur_solve_batched(int nprob, gs_ctx* const* ctxs, const int* type, c
                 const size_t off = (size_t)j * ctxs[i]->V * kSiteC;
                 const int old_cap = c->coop_block_cap;
                 c->coop_block_cap = ctxs[i]->opt_coop_blocks;
-                c->batch_running = lanes > 1 ? &running : nullptr;
+                if (lanes > 1) {
+                    ledger_enter(&ledger, c);
+                    c->ledger = &ledger;
+                }
                 s = schur_solve(c, type[i], dir[i], inverse[i], (const double2*)f_dev[i] + off,
                                 (double2*)x_dev[i] + off, opts, &sj);
                 if (cudaStreamSynchronize(c->stream) != cudaSuccess && s == GS_OK) {
                     const cudaError_t e = cudaGetLastError();
                     s = set_err(c, GS_ECUDA, "schur_solve_batched: %s", cudaGetErrorString(e));
                 }
-                c->batch_running = nullptr;
+                if (lanes > 1) {
+                    c->ledger = nullptr;
+                    ledger_leave(&ledger, c);
+                }
                 c->coop_block_cap = old_cap;
                 if (s != GS_OK && s != GS_MAXITER && c != ctxs[i]) m = c->err;
             }
             {
                 std::lock_guard<std::mutex> lk(mu);
-                running.fetch_sub(1);
                 busy[i][slot] = 0;
                 merge_stats(sts[i], sj);
                 if (s != GS_OK && s != GS_MAXITER && msg[i].empty()) msg[i] = m.empty() ? "-" : m;

@@ -8,6 +8,8 @@
 #include <string.h>
 
 #include <atomic>
+#include <condition_variable>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -180,6 +182,39 @@ struct OuterWork {
 
 }  // namespace gs
 
+struct gs_ctx;
+
+namespace gs {
+// The blocks of the persistent solver kernels of one schur_solve_batched
+// call.  Those kernels all have 128 threads and the same registers, so their
+// blocks are interchangeable and the GPU holds per_sm x SMs of them at once.
+// held[] records, per running solve, the blocks its kernel may have in
+// flight: its last grid (its previous kernel has finished before it launches
+// again), or nothing before its first launch.  A grid is granted only from
+// blocks no other solve holds, so the cooperative grids of all running
+// solves always fit on the GPU together; a solve that has not launched yet
+// is counted at `reserve` when the others are granted blocks, so it finds
+// room at its first launch.
+struct BlockLedger {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::atomic<int> running{0};
+    int64_t reserve = 1;
+    struct Entry {
+        const gs_ctx* ctx;
+        int64_t blocks;
+        bool launched;
+    };
+    std::vector<Entry> held;
+};
+void ledger_enter(BlockLedger* L, const gs_ctx* c);
+void ledger_leave(BlockLedger* L, const gs_ctx* c);
+// blocks for c's next cooperative grid: at most want and target, never more
+// than the others leave free; 0 if none became free within the context's
+// wait limit x 60
+int64_t ledger_grant(gs_ctx* c, int per_sm, int64_t want, int64_t target);
+}  // namespace gs
+
 struct gs_ctx {
     int dims[4];
     int64_t V = 0;
@@ -210,10 +245,9 @@ struct gs_ctx {
     void* persist = nullptr;           // persistent-solver scratch (persistent.cu)
     void* multi = nullptr;             // multi-RHS workspaces (multi.cu)
     int coop_block_cap = 0;            // cap on cooperative grids (0 = whole GPU; batched solves)
-    // batched solves: the number of solves running at once, shared by the
-    // contexts of one schur_solve_batched call (null outside such a call);
-    // each cooperative grid takes its share of the GPU when it is launched
-    const std::atomic<int>* batch_running = nullptr;
+    // batched solves: the block ledger of the schur_solve_batched call this
+    // context is running an item of (null outside such a call)
+    gs::BlockLedger* ledger = nullptr;
     int opt_batch_lanes = 0;           // concurrent solves of schur_solve_batched (0 = the library's choice)
     std::vector<gs_ctx*> lanes;        // extra contexts on the same lattice for schur_solve_batched
     cudaStream_t own_stream = nullptr; // a stream the library created for this context (lane contexts)
@@ -249,8 +283,8 @@ constexpr int64_t kBatchMaxRestSites = 16384;
 inline int64_t coop_blocks(const gs_ctx* c, int per_sm, int64_t rest_sites) {
     int64_t g = (int64_t)per_sm * c->num_sms;
     if (c->coop_block_cap > 0) return g < c->coop_block_cap ? g : c->coop_block_cap;
-    if (c->batch_running) {
-        int n = c->batch_running->load(std::memory_order_relaxed);
+    if (c->ledger) {
+        int n = c->ledger->running.load(std::memory_order_relaxed);
         if (n < 1) n = 1;
         const int64_t per = (rest_sites <= kBatchMaxRestSites && per_sm > 2) ? 2 : per_sm;
         g = per * c->num_sms / n;

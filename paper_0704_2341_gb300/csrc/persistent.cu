@@ -650,14 +650,32 @@ __global__ void __launch_bounds__(kPThreads) k_selftest_grid_timeout(GridSync g,
 }
 
 // co-resident grid for a cooperative launch on a set of rest_sites sites: at
-// most `want` blocks
+// most `want` blocks.  Inside schur_solve_batched (no GS_OPT_COOP_BLOCKS) the
+// grid comes from the call's block ledger: on a small rest set a kernel that
+// passes `round` (the blocks for one round of its tiles) asks for exactly
+// that -- on 8^4 the four permutations' FP64 solves take 120 + 64 + 120 + 64
+// of the 456 co-resident blocks, one tile round per stencil phase each
+// (45.0 solves/s against 40.2 with 76 blocks each); otherwise it asks for its
+// share of the GPU while n solves run (two blocks per SM on small sets, all
+// co-resident blocks on large ones).
 template <class K>
-static int coop_grid(gs_ctx* c, K kernel, int64_t want, int64_t rest_sites) {
+static int coop_grid(gs_ctx* c, K kernel, int64_t want, int64_t rest_sites, int64_t round = 0) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPThreads, 0) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         return 0;
+    }
+    const int64_t full = (int64_t)per_sm * c->num_sms;
+    if (c->ledger && c->coop_block_cap == 0) {
+        int64_t w = want < full ? want : full;
+        if (w > kMaxRedBlocks) w = kMaxRedBlocks;
+        if (w < 1) w = 1;
+        const int n = c->ledger->running.load() > 1 ? c->ledger->running.load() : 1;
+        const bool small = rest_sites <= kBatchMaxRestSites;
+        const int64_t target = (small && round > 0) ? round
+                               : (small && per_sm > 2 ? 2 : per_sm) * (int64_t)c->num_sms / n;
+        return (int)ledger_grant(c, per_sm, w, target > 0 ? target : 1);
     }
     int64_t g = coop_blocks(c, per_sm, rest_sites);
     if (want < g) g = want;
@@ -707,7 +725,7 @@ gs_status persistent_bicg_f64(gs_ctx* c, const StencilArgs& A, const StencilArgs
     if (s != GS_OK) return s;
     const int64_t tiles = (A.n_out + kSitesPerBlock - 1) / kSitesPerBlock;
     const int64_t want = tiles > (int64_t)c->num_sms ? tiles : (int64_t)c->num_sms;
-    const int g = coop_grid(c, k_bicg_persistent_f64, want, A.n_out);
+    const int g = coop_grid(c, k_bicg_persistent_f64, want, A.n_out, tiles);
     if (g < 1) return set_err(c, GS_ECUDA, "no co-resident grid for the persistent solver");
     // tiles of up to 32 sites, no more than the grid needs to cover the rest set
     // once (3840 sites on 152 blocks: 26 per tile, so every SM shares the work)
