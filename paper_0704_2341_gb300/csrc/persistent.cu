@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(kPThreads) k_selftest_grid_timeout(GridSync g,
 // co-resident grid for a cooperative launch on a set of rest_sites sites: at
 // most `want` blocks.  Inside schur_solve_batched (no GS_OPT_COOP_BLOCKS) the
 // grid comes from the call's block ledger: on a small rest set a kernel that
-// passes `round` (the blocks for one round of its tiles) asks for exactly
+// passes `round` (the blocks for one pass over the set) asks for exactly
 // that -- on 8^4 the four permutations' FP64 solves take 120 + 64 + 120 + 64
 // of the 456 co-resident blocks, one tile round per stencil phase each
 // (45.0 solves/s against 40.2 with 76 blocks each); otherwise it asks for its
@@ -776,7 +776,10 @@ static gs_status persistent_bicg_lp_t(gs_ctx* c, const LpArgs& A, const LpArgs& 
     if (s != GS_OK) return s;
     const int64_t blocks = (n + kPThreads - 1) / kPThreads;
     const int64_t want = blocks > (int64_t)c->num_sms ? blocks : (int64_t)c->num_sms;
-    const int g = coop_grid(c, k_bicg_persistent_lp<S>, want, n);
+    // in a batched call on a small set: one pass with about 96 sites per block
+    // (8^4, four FP32-inner solves at once: 87.1 solves/s with 40 + 24 + 40 +
+    // 24 blocks, 84.9 with one full 128-site round, 75.8 with 76 blocks each)
+    const int g = coop_grid(c, k_bicg_persistent_lp<S>, want, n, (n + 95) / 96);
     if (g < 1) return set_err(c, GS_ECUDA, "no co-resident grid for the persistent solver");
     GS_CUDA(c, cudaMemsetAsync(ps->words, 0, 4 * sizeof(unsigned int), c->stream));
     PArgsLp P;
