@@ -820,8 +820,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     Ud = torch.from_numpy(U).to(dev)
     # one context and stream per permutation: a step solves the four systems
-    # at once (schur_solve_batched; each solve's persistent kernels on its
-    # share of the SMs)
+    # at once (schur_solve_batched; each solve's persistent kernels granted
+    # one tile round by the call's block ledger)
     pstreams = [torch.cuda.Stream(device=dev) for _ in PERMS]
     ctxs = []
     for ps in pstreams:
@@ -1023,8 +1023,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "solves_per_step": len(PERMS),
                    "form": "plain FP64; the four permutations' solves at once (schur_solve_batched: one "
-                           "context and stream per permutation, each solve's persistent kernels on a "
-                           "quarter of the SMs)",
+                           "context and stream per permutation, each solve's persistent kernels granted "
+                           "one round of 32-site tiles, 120 or 64 of the 456 co-resident blocks, by the "
+                           "call's block ledger)",
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "max_true_residual": worst},
