@@ -58,10 +58,9 @@ TABLE1_LEVELS = {5.4: [(1, 0, 1), (1, 0, 1)], 5.7: [(1, 0, 1), (1, 0, 1)],
 TABLE1_PAPER = {5.4: (57, 0.76, 0.05), 5.7: (480, 0.83, 0.16), 5.9: (905, 0.89, 0.48)}
 PERM_NAMES = ["P_I", "P_II", "P_I^T", "P_II^T"]
 # DRAM traffic per launch from one ncu capture, per profiled kernel family
-# (0: the FP64 stencil, 3: the persistent FP64 BiCGStab), with the hash of the
-# sources it was taken on
-NCU_SUMMARY = {0: (os.path.join(ROOT, "profiles", "dslash_f64_8x4_traffic.txt"), ("dslash_f64.cu",)),
-               3: (os.path.join(ROOT, "profiles", "bicg_persistent_f64_8x4_traffic.txt"),
+# (3: the persistent FP64 BiCGStab, the step's dominant kernel), with the hash
+# of the sources it was taken on; other families report no traffic
+NCU_SUMMARY = {3: (os.path.join(ROOT, "profiles", "bicg_persistent_f64_8x4_traffic.txt"),
                    ("persistent.cu", "dslash_f64.cuh", "gridsync.cuh"))}
 
 
