@@ -167,9 +167,12 @@ enum { GS_OPT_STENCIL_VARIANT = 1, GS_OPT_INNER_KERNEL = 2, GS_OPT_NET_KERNEL = 
  * stays usable.
  * GS_OPT_COOP_BLOCKS: the number of blocks the persistent (cooperative)
  * solver kernels of this problem use while schur_solve_batched runs several
- * solves at once; 0 = sized at each launch for 1/n of the GPU while n solves
- * run -- every co-resident block on rest sets above 16384 sites, two per SM
- * below (the default).
+ * solves at once (the caller then keeps their sum within what the GPU holds
+ * at once); 0 = granted at each launch by the call's block ledger (the
+ * default): on rest sets of at most 16384 sites one pass over the set (FP64:
+ * one round of 32-site tiles; FP32 / BF16: about 96 sites per block), above
+ * that an even share of the co-resident blocks among the running solves,
+ * never more than the other solves leave free.
  * GS_OPT_BATCH_LANES (read from the first problem's context): how many solves
  * schur_solve_batched runs at once, 1 .. 64; 0 = four (the default). */
 gs_status gs_set_option(gs_ctx* ctx, int option, int value);
@@ -356,8 +359,9 @@ gs_status schur_solve_multi(gs_ctx* ctx, int type, int dir, int inverse, int nrh
  * the problem's context and released by gs_destroy; several GB on large
  * lattices; its field is copied again after gs_set_gauge).  With the
  * network inner solver (GS_INNER_FGMRES_NET) a problem's sources run on its
- * own context only.  While n solves run, each persistent kernel takes 1/n
- * of the GPU when launched (GS_OPT_COOP_BLOCKS).  The callers' streams are
+ * own context only.  The running solves' persistent kernels draw their
+ * blocks from one ledger, so their cooperative grids always fit on the GPU
+ * together (GS_OPT_COOP_BLOCKS).  The callers' streams are
  * synchronised before the first solve, every lane stream before return.  The
  * contexts must be distinct (they may hold the same lattice and field).
  * stats (may be NULL): nprob entries, each aggregating its problem's sources
