@@ -307,8 +307,55 @@ def kernel_case(args):
     if args.case == "net_tc":
         print(json.dumps(net_case(dims, args.reps)), flush=True)
         return
+    if args.case == "lp_solve":
+        print(json.dumps(lp_solve_case(dims, args.prec, args.reps)), flush=True)
+        return
     out = stencil_roofline(args.case, dims, args.prec, args.variant, args.reps)
     print(json.dumps(out), flush=True)
+
+
+def lp_solve_case(dims, prec_name="f32", reps=3):
+    """One mixed-precision inner D_rr solve (Type I rest set; FP32 or BF16
+    storage; persistent low-precision BiCGStab cycles with FP64 defect
+    correction, to 1e-10) on a lattice larger than L2 (exp(i 0.2 H) field, seed
+    3, m0 = -0.35): the achieved algorithmic bytes/s of k_bicg_persistent_lp,
+    from the library's CUDA-event profiling of its launches, against the
+    measured HBM copy bandwidth (the command of its profile)."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_0704_2341_gb300 as gs
+    from lattice_inputs import torchgen
+    import lattice_inputs as li
+    V = li.volume(dims)
+    stream = torch.cuda.current_stream()
+    ctx = gs.Context(dims, -0.35, stream.cuda_stream)
+    ctx.set_gauge(torchgen.random_gauge_t(dims, 0.2, 3, "cuda"))
+    nr = V - ctx.get_permutation(1, 0, 0, torch.empty(V, dtype=torch.int32, device="cuda"))
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    t = torch.randn(nr * 12, dtype=torch.complex128, device="cuda", generator=gen)
+    z = torch.empty_like(t)
+    prec = gs.GS_F32 if prec_name == "f32" else gs.GS_BF16
+    o = gs.gs_default_opts(inner_prec=prec, inner_tol=1e-10)
+    ctx.solve_rr(1, 0, 0, t, z, o)      # warm-up: plans, stencil tuning, workspaces
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    iters = 0
+    for _ in range(reps):
+        st = ctx.solve_rr(1, 0, 0, t, z, o)
+        iters += st.inner_iters
+    p = ctx.profile_read(gs.GS_PROF_SOLVER_LP)
+    ctx.profile(False)
+    peaks = _peaks()
+    ms = p.ms / p.launches
+    gbs = p.bytes / p.launches / (ms / 1e3) / 1e9
+    out = {"case": "lp_solve", "dims": dims, "prec": prec_name, "rest_sites": nr, "solves": reps,
+           "inner_iterations_per_solve": iters / reps, "launches": p.launches,
+           "us_per_launch": 1e3 * ms, "algorithmic_bytes_per_launch": p.bytes / p.launches,
+           "gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+           "inner_residual": st.inner_residual}
+    ctx.close()
+    return out
 
 
 def stencil_roofline(case, dims, prec_name="f32", variant=0, reps=20):
@@ -788,7 +835,7 @@ def main():
     ap.add_argument("--only", default=None,
                     choices=["batched", "learned_large", "reusken", "table1", "mixed_large"],
                     help="run one section alone and print it")
-    ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp", "net_tc"],
+    ap.add_argument("--case", default=None, choices=["wilson_f64", "wilson_lp", "net_tc", "lp_solve"],
                     help="kernel micro-benchmark instead of the solve (for profiling)")
     ap.add_argument("--prec", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
