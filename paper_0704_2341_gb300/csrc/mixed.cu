@@ -829,7 +829,13 @@ gs_status inner_solve_mixed(gs_ctx* c, const Plan* p, const double2* t, double2*
         gs_solve_stats sub;
         memset(&sub, 0, sizeof sub);
         st.lowp_fallbacks += 1;
+        // inside a batched call the block ledger counts only the low-precision
+        // solver's cooperative blocks: the FP64 fallback there runs one launch
+        // per phase instead of a cooperative grid of another block size
+        const int keep_kernel = c->opt_inner_kernel;
+        if (c->ledger) c->opt_inner_kernel = 1;
         gs_status si = inner_solve_f64(c, p, r64, m->e64, o64, sub);
+        c->opt_inner_kernel = keep_kernel;
         st.inner_iters += sub.inner_iters;
         if (si != GS_OK && si != GS_MAXITER) return si;
         if ((s = launch_axpby(c, make_double2(1.0, 0.0), m->e64, make_double2(1.0, 0.0), z,

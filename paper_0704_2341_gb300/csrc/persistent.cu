@@ -427,12 +427,13 @@ __device__ __forceinline__ float2 fdiv2(float2 a, float2 b) {
     return make_float2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
 }
 
-// MINB: blocks per SM the register budget is set for -- 4 (128 registers) for
-// a solve that has the GPU to itself, 3 (at most 168 registers, the
-// footprint of the FP64 solver) inside a batched call, whose block ledger
-// counts every persistent block alike
-template <class S, int MINB>
-__global__ void __launch_bounds__(kPThreads, MINB) k_bicg_persistent_lp(PArgsLp P) {
+// Register budget for four blocks per SM (128 registers; 24^3 x 48, FP32:
+// 0.69 of measured HBM against 0.65 at the compiler's 164 and three per SM).
+// In a batched call with low-precision inner solves these are the only
+// cooperative blocks (the FP64 fallback runs one launch per phase there), so
+// the call's block ledger still counts blocks of one size.
+template <class S>
+__global__ void __launch_bounds__(kPThreads, 4) k_bicg_persistent_lp(PArgsLp P) {
     __shared__ float2 sc[4];  // alpha, omega, beta, rho
     __shared__ int s_flag;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -780,10 +781,7 @@ static gs_status persistent_bicg_lp_t(gs_ctx* c, const LpArgs& A, const LpArgs& 
     if (s != GS_OK) return s;
     const int64_t blocks = (n + kPThreads - 1) / kPThreads;
     const int64_t want = blocks > (int64_t)c->num_sms ? blocks : (int64_t)c->num_sms;
-    // alone, four blocks per SM (24^3 x 48, FP32: 0.69 of measured HBM
-    // against 0.65 with three); in a batched call three, like every other
-    // persistent kernel there
-    void (*kern)(PArgsLp) = c->ledger ? k_bicg_persistent_lp<S, 3> : k_bicg_persistent_lp<S, 4>;
+    void (*kern)(PArgsLp) = k_bicg_persistent_lp<S>;
     // in a batched call on a small set: one pass with about 96 sites per block
     // (8^4, four FP32-inner solves at once: 87.1 solves/s with 40 + 24 + 40 +
     // 24 blocks, 84.9 with one full 128-site round, 75.8 with 76 blocks each)
